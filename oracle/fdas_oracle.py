@@ -1,0 +1,294 @@
+"""FP64 CPU oracle of the Fourier Domain Acceleration Search hot path.
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE. Only the test suite, the smoke check
+in ``__graft_entry__`` and the CPU-baseline leg of ``bench.py`` may import
+this module. It shares no code with the CUDA path and is deliberately plain
+and slow: whole-array numpy/scipy steps in float64, in the order the paper
+gives them (Section 4, steps 2-7), followed by the harmonic sum and the
+threshold that the search adds after the power plane.
+
+Pins: every function here is checked in ``tests/test_oracle_pins.py``
+against something other than itself (closed forms, brute force on tiny
+inputs, Euler-Maclaurin error terms, invariants); see the docstrings.
+
+Readings of the paper used here (the paper is silent or garbled on them):
+  * Eq. 1 has m+1 terms and a garbled index; the plane is read as m taps,
+    A(r, z) = sum_{d=-m/2}^{m/2-1} Xw[r+d] * tau_z(d).
+  * tau_z is the conjugated response of a constant-acceleration signal whose
+    *mean* frequency is r (template centred on d = 0), Section 2; z = fdot T^2
+    with T the observation length.
+  * the spectrum keeps bins 0..N/2-1 (Nyquist dropped); whitening is a
+    64-bin running median (the step is not in the paper).
+  * harmonic sums use round-half-up in r and round-half-away-from-zero in
+    the centred z index; the threshold is the Gamma(h, 1) tail that equals
+    the one-sided Gaussian tail at ``sigma``.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import special
+
+LN2 = math.log(2.0)
+MEDIAN_WINDOW = 64
+
+
+# ----------------------------------------------------------------------------
+# Grid helpers (Section 2: z = fdot * T^2 templates, spaced dz apart)
+# ----------------------------------------------------------------------------
+def n_templates(zmax: int, dz: int) -> int:
+    return 2 * (zmax // dz) + 1
+
+
+def z_values(zmax: int, dz: int) -> np.ndarray:
+    return -zmax + dz * np.arange(n_templates(zmax, dz), dtype=np.float64)
+
+
+# ----------------------------------------------------------------------------
+# Step 2 (Section 4): real-to-complex DFT of the series.
+# ----------------------------------------------------------------------------
+def spectrum(x: np.ndarray) -> np.ndarray:
+    """X_k = sum_n x_n exp(-2 pi i k n / N), k = 0 .. N/2-1 (Nyquist dropped).
+
+    numpy's FFT is the library step; pinned against a direct DFT sum.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    return np.fft.rfft(x)[: x.shape[0] // 2]
+
+
+# ----------------------------------------------------------------------------
+# Spectral whitening (not in the paper; added by the search contract).
+# ----------------------------------------------------------------------------
+def window_start(k: np.ndarray, nb: int, w: int = MEDIAN_WINDOW) -> np.ndarray:
+    """First bin of the w-bin median window of bin k: [k-w/2, k+w/2-1],
+    shifted (not shrunk) so that it lies inside [1, nb-1]."""
+    return np.clip(np.asarray(k) - w // 2, 1, nb - w)
+
+
+def running_median_power(X: np.ndarray, w: int = MEDIAN_WINDOW) -> np.ndarray:
+    """mu_k = even-count median (mean of the two middle order statistics) of
+    |X|^2 over the window of bin k; mu_0 is unused (returned as nan)."""
+    nb = X.shape[0]
+    if nb < w + 1:
+        raise ValueError("spectrum too short for the median window")
+    p = np.abs(X) ** 2
+    n_starts = nb - w                     # starts 1 .. nb-w
+    med = np.empty(n_starts + 1)
+    med[0] = np.nan
+    view = np.lib.stride_tricks.sliding_window_view(p[1:], w)  # rows = starts
+    chunk = 1 << 16
+    for a in range(0, n_starts, chunk):
+        b = min(a + chunk, n_starts)
+        part = np.partition(view[a:b], [w // 2 - 1, w // 2], axis=1)
+        med[1 + a: 1 + b] = 0.5 * (part[:, w // 2 - 1] + part[:, w // 2])
+    mu = np.empty(nb)
+    mu[0] = np.nan
+    k = np.arange(1, nb)
+    mu[1:] = med[window_start(k, nb, w)]
+    return mu
+
+
+def whiten(X: np.ndarray, w: int = MEDIAN_WINDOW) -> np.ndarray:
+    """Xw_k = X_k * sqrt(ln 2 / mu_k), Xw_0 = 0.
+
+    For complex Gaussian noise |X|^2 is exponential and its median is
+    ln 2 times its mean, so whitened noise has unit mean power.
+    """
+    mu = running_median_power(X, w)
+    Xw = np.zeros_like(X, dtype=np.complex128)
+    Xw[1:] = X[1:] * np.sqrt(LN2 / mu[1:])
+    return Xw
+
+
+# ----------------------------------------------------------------------------
+# Templates (Section 2; the response of Ransom et al. 2002, which Eq. 1 uses)
+# ----------------------------------------------------------------------------
+def template_fresnel(z: float, m: int, offset: float = 0.0) -> np.ndarray:
+    """tau_z(d) = int_0^1 exp(2 pi i [(d - offset + z/2) u - z u^2 / 2]) du for
+    d = -m/2 .. m/2-1, via the Fresnel integrals C, S (scipy, float64).
+    ``offset`` evaluates the response at a fractional frequency r + offset.
+
+    Completing the square with q = d - offset + z/2, s_a = sqrt(2|z|)(a - q/z):
+        tau = conj( exp(-i pi q^2/z) [dC + i sgn(z) dS] ) / sqrt(2|z|),
+    dC = C(s_1) - C(s_0), dS = S(s_1) - S(s_0). For z = 0 the integral is
+    (exp(2 pi i q) - 1) / (2 pi i q), i.e. delta_{d,0} at zero offset.
+    """
+    d = np.arange(-m // 2, m // 2, dtype=np.float64)
+    if z == 0:
+        q = d - offset
+        out = np.ones(m, dtype=np.complex128)
+        nz = q != 0
+        out[nz] = (np.exp(2j * np.pi * q[nz]) - 1.0) / (2j * np.pi * q[nz])
+        if offset == 0.0:
+            out = (d == 0).astype(np.complex128)
+        return out
+    q = d - offset + z / 2.0
+    scale = math.sqrt(2.0 * abs(z))
+    s0 = scale * (0.0 - q / z)
+    s1 = scale * (1.0 - q / z)
+    S0, C0 = special.fresnel(s0)
+    S1, C1 = special.fresnel(s1)
+    dF = (C1 - C0) + 1j * np.sign(z) * (S1 - S0)
+    # exp(-i pi q^2 / z) with the argument reduced exactly: q^2/z = Q^2/(4z),
+    # Q = 2q an integer whenever z is an integer.
+    Q = np.rint(2.0 * q).astype(np.int64)
+    if offset == 0.0 and float(z).is_integer():
+        zi = int(z)
+        red = np.mod(Q * Q, 8 * abs(zi)) / (4.0 * abs(zi))     # in [0, 2)
+        ph = np.exp(-1j * np.pi * red * np.sign(zi))
+    else:
+        ph = np.exp(-1j * np.pi * q * q / z)
+    return np.conj(ph * dF) / scale
+
+
+def template_discrete(z: float, m: int, n: int) -> np.ndarray:
+    """Exact DFT-domain response of a sampled chirp of length n:
+    tau_z(d) = (1/n) sum_k exp(2 pi i [(d + z/2) k/n - z k^2/(2 n^2)]),
+    for d = -m/2 .. m/2-1 (one float64 inverse FFT of the chirp)."""
+    k = np.arange(n, dtype=np.float64)
+    cyc = (z / 2.0) * k / n - z * k * k / (2.0 * n * n)
+    cyc -= np.floor(cyc)
+    u = np.exp(2j * np.pi * cyc)
+    t = np.fft.ifft(u)
+    d = np.arange(-m // 2, m // 2)
+    return t[np.mod(d, n)]
+
+
+def template_bank(zmax: int, dz: int, m: int) -> np.ndarray:
+    """(Z, m) complex128 taps tau_{z_j}(d), rows j = 0..Z-1, z_j = -zmax + j dz."""
+    return np.stack([template_fresnel(z, m) for z in z_values(zmax, dz)])
+
+
+# ----------------------------------------------------------------------------
+# Steps 3-7 (Section 4) as their definition: the f-fdot power plane.
+# ----------------------------------------------------------------------------
+def correlate_row(Xw: np.ndarray, tau: np.ndarray) -> np.ndarray:
+    """A(r) = sum_{d=-m/2}^{m/2-1} Xw[r+d] tau(d), r = 0..nb-1, Xw = 0 outside
+    [0, nb). One zero-padded FFT correlation over the whole spectrum (no
+    segmenting): FFT(A) = FFT(Xw_pad) * conj(FFT(conj(g))), g[d mod Lc] = tau(d).
+    """
+    nb = Xw.shape[0]
+    m = tau.shape[0]
+    lc = 1
+    while lc < nb + m:
+        lc *= 2
+    a = np.zeros(lc, dtype=np.complex128)
+    a[:nb] = Xw
+    g = np.zeros(lc, dtype=np.complex128)
+    d = np.arange(-m // 2, m // 2)
+    g[np.mod(d, lc)] = tau
+    c = np.fft.ifft(np.fft.fft(a) * np.conj(np.fft.fft(np.conj(g)))) * 1.0
+    return c[:nb]
+
+
+def power_plane(Xw: np.ndarray, taus: np.ndarray) -> np.ndarray:
+    """P[j, r] = |A_j(r)|^2, shape (Z, nb), float64 (step 7: powers)."""
+    return np.stack([np.abs(correlate_row(Xw, t)) ** 2 for t in taus])
+
+
+def plane_cells(Xw: np.ndarray, taus: np.ndarray, j_idx, r_idx) -> np.ndarray:
+    """Direct sums of Eq. 1 at individual cells (j, r): for full-size checks."""
+    nb = Xw.shape[0]
+    m = taus.shape[1]
+    d = np.arange(-m // 2, m // 2)
+    j_idx = np.asarray(j_idx)
+    r_idx = np.asarray(r_idx)
+    out = np.empty(j_idx.shape[0])
+    for i, (j, r) in enumerate(zip(j_idx, r_idx)):
+        idx = r + d
+        ok = (idx >= 0) & (idx < nb)
+        out[i] = abs(np.sum(Xw[idx[ok]] * taus[j][ok])) ** 2
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Harmonic sum and threshold (added after step 7 by the search contract).
+# ----------------------------------------------------------------------------
+def harmonic_levels(nharm: int):
+    out, h = [], 1
+    while h <= nharm:
+        out.append(h)
+        h *= 2
+    return out
+
+
+def subharmonic_r(r, k: int, h: int):
+    """round(k r / h), ties up: floor((2 k r + h) / (2 h))."""
+    return (2 * k * np.asarray(r, dtype=np.int64) + h) // (2 * h)
+
+
+def subharmonic_j(j, k: int, h: int, zc: int):
+    """zc + round(k (j - zc) / h), ties away from zero (keeps z symmetry)."""
+    jc = np.asarray(j, dtype=np.int64) - zc
+    a = np.abs(k * jc)
+    return zc + np.sign(jc) * ((2 * a + h) // (2 * h))
+
+
+def harmonic_sums(P: np.ndarray, nharm: int) -> dict:
+    """H_h[j, r] = sum_{k=1..h} P[jz(k, j, h), rr(k, r, h)] for h = 1, 2, 4..nharm."""
+    Z, nb = P.shape
+    zc = (Z - 1) // 2
+    r = np.arange(nb)
+    j = np.arange(Z)
+    out = {}
+    for h in harmonic_levels(nharm):
+        H = np.zeros_like(P)
+        for k in range(1, h + 1):
+            H += P[np.ix_(subharmonic_j(j, k, h, zc), subharmonic_r(r, k, h))]
+        out[h] = H
+    return out
+
+
+def gaussian_tail(sigma: float) -> float:
+    """One-sided Gaussian tail probability of a sigma-sigma excess."""
+    return 0.5 * math.erfc(sigma / math.sqrt(2.0))
+
+
+def thresholds(nharm: int, sigma: float = 6.0) -> dict:
+    """T_h with P(Gamma(h, 1) >= T_h) = gaussian_tail(sigma): the sum of h
+    whitened noise powers (each exponential with unit mean) is Gamma(h, 1)."""
+    p = gaussian_tail(sigma)
+    return {h: float(special.gammainccinv(h, p)) for h in harmonic_levels(nharm)}
+
+
+def candidates(P: np.ndarray, nharm: int, sigma: float = 6.0):
+    """All (r, j, h, H) with r >= 1 and H_h(r, j) >= T_h, sorted by (h, r, j)."""
+    T = thresholds(nharm, sigma)
+    H = harmonic_sums(P, nharm)
+    rows = []
+    for h in harmonic_levels(nharm):
+        jj, rr = np.nonzero(H[h][:, 1:] >= T[h])
+        rr = rr + 1
+        for a, b in zip(rr, jj):
+            rows.append((int(a), int(b), h, float(H[h][b, a])))
+    rows.sort(key=lambda t: (t[2], t[0], t[1]))
+    return rows, H
+
+
+def harmonic_sum_cells(Xw, taus, nharm: int, j_idx, r_idx) -> dict:
+    """H_h at individual top cells from direct plane-cell sums (full-size checks)."""
+    Z = taus.shape[0]
+    zc = (Z - 1) // 2
+    out = {}
+    for h in harmonic_levels(nharm):
+        acc = np.zeros(len(j_idx))
+        for k in range(1, h + 1):
+            acc += plane_cells(Xw, taus, subharmonic_j(j_idx, k, h, zc),
+                               subharmonic_r(r_idx, k, h))
+        out[h] = acc
+    return out
+
+
+# ----------------------------------------------------------------------------
+# The whole path on one series.
+# ----------------------------------------------------------------------------
+def search(x: np.ndarray, zmax: int, dz: int, m: int, nharm: int,
+           sigma: float = 6.0):
+    """Returns (Xw, taus, P, candidate rows, harmonic sums)."""
+    X = spectrum(x)
+    Xw = whiten(X)
+    taus = template_bank(zmax, dz, m)
+    P = power_plane(Xw, taus)
+    cands, H = candidates(P, nharm, sigma)
+    return Xw, taus, P, cands, H

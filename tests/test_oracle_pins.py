@@ -1,0 +1,312 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test ties one oracle function to a closed form, an exact identity,
+brute force on a tiny input, an Euler-Maclaurin error term or a statistical
+law, chosen so that a dropped term, a flipped sign, a shifted index or a
+transposed operand in the oracle fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fdas_oracle as O
+from synthetic import Chirp, make_series, workload
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- spectrum --
+def test_spectrum_matches_direct_dft():
+    """Step 2 (Section 4): brute-force DFT sum on a tiny series."""
+    rng = np.random.default_rng(3)
+    n = 48
+    x = rng.standard_normal(n)
+    X = O.spectrum(x)
+    assert X.shape == (n // 2,)
+    for k in range(n // 2):
+        ref = sum(x[t] * complex(math.cos(2 * math.pi * k * t / n),
+                                 -math.sin(2 * math.pi * k * t / n)) for t in range(n))
+        assert abs(X[k] - ref) < 1e-12 * n
+
+
+# ------------------------------------------------------------- templates --
+@pytest.mark.parametrize("n", [1 << 12, 1 << 14])
+@pytest.mark.parametrize("z", [-50.0, -7.0, -2.0, 2.0, 36.0, 50.0])
+def test_fresnel_template_vs_discrete_euler_maclaurin(n, z):
+    """Section 2 template. The exact response of a sampled chirp is the
+    left-endpoint sum (1/n) sum_k f(k/n) of the integrand f of the continuous
+    template. Because f(1) = f(0) for integer d, Euler-Maclaurin gives
+    discrete - continuous = (f'(1) - f'(0)) / (12 n^2) + O(n^-4)
+                          = -i pi z / (6 n^2) + O(n^-4)."""
+    m = 128
+    tf = O.template_fresnel(z, m)
+    td = O.template_discrete(z, m, n)
+    pred = -1j * math.pi * z / (6.0 * n * n)
+    resid = np.max(np.abs(td - tf - pred))
+    bound = 2.0 * (2 * math.pi * (m / 2 + abs(z))) ** 3 / (720.0 * n ** 4)
+    assert resid <= bound + 1e-14, (resid, bound)
+    # the leading term itself is visible (the closed form is not accidentally
+    # equal to the discrete sum for a wrong reason)
+    assert np.max(np.abs(td - tf)) > 0.5 * abs(pred)
+
+
+@pytest.mark.parametrize("z", [-6.0, 0.0, 4.0, 5.0])
+def test_full_width_discrete_template_equals_brute_force_chirped_dft(z):
+    """With all n taps of the discrete template, the correlation
+    sum_d X[r+d] tau_z(d) (circular over the complex spectrum) equals the
+    brute-force chirped DFT sum_n x_n exp(-2 pi i ((r - z/2) n/n + z n^2/(2 n^2)))
+    exactly; r labels the chirp's mean frequency."""
+    n = 64
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    X = np.fft.fft(x)
+    tau = O.template_discrete(z, n, n)
+    d = np.arange(-n // 2, n // 2)
+    t = np.arange(n)
+    for r in (0, 3, 10, 40, 63):
+        corr = np.sum(X[np.mod(r + d, n)] * tau)
+        bf = np.sum(x * np.exp(-2j * np.pi * ((r - z / 2) * t / n + z * t * t / (2.0 * n * n))))
+        assert abs(corr - bf) <= 1e-12 * abs(bf) + 1e-12
+
+
+@pytest.mark.parametrize("z", [-40.0, -2.0, 2.0, 30.0])
+def test_template_parseval_and_symmetry(z):
+    """sum over all d of |tau_z(d)|^2 = int_0^1 |f|^2 = 1 (Parseval for the
+    Fourier coefficients of a unit-modulus function); the tail beyond |d| = M
+    decays like 1/(pi d)^2. And tau_{-z}(d) = conj(tau_z(-d))."""
+    m = 1 << 14
+    t = O.template_fresnel(z, m)
+    s = np.sum(np.abs(t) ** 2)
+    assert abs(s - 1.0) < 4.0 / (math.pi ** 2 * (m / 2 - abs(z)))
+    tn = O.template_fresnel(-z, 512)
+    tp = O.template_fresnel(z, 512)
+    # index i <-> d = i - 256; -d <-> 512 - i (valid for i >= 1)
+    assert np.max(np.abs(tn[1:] - np.conj(tp[1:][::-1]))) < 1e-14
+
+
+def test_template_discrete_parseval_exact():
+    n = 256
+    t = O.template_discrete(14.0, n, n)
+    assert abs(np.sum(np.abs(t) ** 2) - 1.0) < 1e-12
+
+
+def test_z0_template_is_fourier_interpolation():
+    """z = 0: integer offset gives tau = delta (plane row = |Xw|^2); a
+    half-bin offset recovers the power of a tone lying halfway between bins
+    (standard Fourier interpolation), which the bare bin underestimates by
+    the scalloping factor 4/pi^2."""
+    n = 4096
+    f = 700.5
+    t = np.arange(n)
+    x = np.cos(2 * np.pi * f * t / n)
+    X = O.spectrum(x)
+    tau_half = O.template_fresnel(0.0, 256, offset=0.5)
+    d = np.arange(-128, 128)
+    r = 700
+    a = np.sum(X[r + d] * tau_half)
+    p_interp = abs(a) ** 2 / (n / 2) ** 2
+    p_bin = abs(X[r]) ** 2 / (n / 2) ** 2
+    assert abs(p_interp - 1.0) < 0.01
+    assert abs(p_bin - 4 / math.pi ** 2) < 0.01
+    assert np.array_equal(O.template_fresnel(0.0, 16), (np.arange(-8, 8) == 0).astype(complex))
+
+
+# ----------------------------------------------------------------- plane --
+def test_correlate_row_matches_direct_loop():
+    """Steps 3-7 as a definition: the FFT correlation against plain loops,
+    including both edges (zero outside [0, nb))."""
+    rng = np.random.default_rng(5)
+    nb, m = 40, 8
+    Xw = rng.standard_normal(nb) + 1j * rng.standard_normal(nb)
+    tau = rng.standard_normal(m) + 1j * rng.standard_normal(m)
+    A = O.correlate_row(Xw, tau)
+    for r in range(nb):
+        acc = 0j
+        for i in range(m):
+            dd = i - m // 2
+            if 0 <= r + dd < nb:
+                acc += Xw[r + dd] * tau[i]
+        assert abs(A[r] - acc) < 1e-12
+
+
+def test_z0_row_of_plane_is_bin_power():
+    rng = np.random.default_rng(6)
+    Xw = rng.standard_normal(300) + 1j * rng.standard_normal(300)
+    taus = O.template_bank(10, 2, 32)
+    P = O.power_plane(Xw, taus)
+    zc = 5
+    assert np.max(np.abs(P[zc] - np.abs(Xw) ** 2)) < 1e-12
+    cells = O.plane_cells(Xw, taus, [0, 3, 10, 7], [0, 150, 299, 17])
+    assert np.allclose(cells, P[[0, 3, 10, 7], [0, 150, 299, 17]], rtol=1e-12, atol=1e-12)
+
+
+def test_noiseless_chirp_peaks_at_injected_cell():
+    """An injected accelerated sinusoid (no noise, unit-noise normalisation)
+    peaks on the grid next to (r0, z0); the true cell's brute-force chirped
+    DFT power is s^2 (amplitude A = 2 s / sqrt(N))."""
+    n = 1 << 17
+    x = make_series(n, 1, [Chirp(10000.3, 35.0, 8.0, 0.3, 1)], noise=False,
+                    dtype=np.float64)
+    t = np.arange(n)
+    bf = abs(np.sum(x * np.exp(-2j * np.pi * ((10000.3 - 17.5) * t / n
+                                              + 35.0 * t * t / (2.0 * n * n))))) ** 2 / n
+    assert abs(bf - 64.0) < 0.01
+    X = O.spectrum(x) / math.sqrt(n)
+    taus = O.template_bank(50, 2, 128)
+    P = O.power_plane(X, taus)
+    j, r = np.unravel_index(np.argmax(P), P.shape)
+    assert r == 10000 and O.z_values(50, 2)[j] == 34.0
+    # scalloping (0.3 bin) and a 1-unit z offset lose part of the power
+    assert 40.0 < P[j, r] < 64.0
+    # at an exactly on-grid signal the plane returns s^2 up to template truncation
+    x2 = make_series(n, 1, [Chirp(10000.0, 34.0, 8.0, 0.3, 1)], noise=False,
+                     dtype=np.float64)
+    P2 = O.plane_cells(O.spectrum(x2) / math.sqrt(n), taus, [42], [10000])
+    assert abs(P2[0] - 64.0) / 64.0 < 0.01
+
+
+def test_cfg1_candidates_contain_injected_signal():
+    x, p = workload("cfg1_n2e17_z50")
+    Xw, taus, P, cands, _ = O.search(x, p["zmax"], p["dz"], p["m"], p["nharm"], p["sigma"])
+    zs = O.z_values(p["zmax"], p["dz"])
+    hits = [c for c in cands if c[2] == 1 and abs(c[0] - 10000) <= 1 and zs[c[1]] in (34.0, 36.0)]
+    assert hits
+    j, r = np.unravel_index(np.argmax(P), P.shape)
+    assert abs(r - 10000) <= 1 and abs(zs[j] - 35.0) <= 2.0
+    # whitened noise has unit mean power (median = ln 2 x mean for an exponential)
+    assert 0.97 < np.mean(np.abs(Xw[1:]) ** 2) < 1.06
+
+
+# ------------------------------------------------------------- whitening --
+def test_whitening_brute_force_small():
+    rng = np.random.default_rng(11)
+    nb = 150
+    X = rng.standard_normal(nb) + 1j * rng.standard_normal(nb)
+    Xw = O.whiten(X)
+    p = [abs(v) ** 2 for v in X]
+    assert Xw[0] == 0
+    for k in range(1, nb):
+        lo = k - 32
+        if lo < 1:
+            lo = 1
+        if lo + 64 > nb:
+            lo = nb - 64
+        win = sorted(p[lo:lo + 64])
+        mu = 0.5 * (win[31] + win[32])
+        assert abs(Xw[k] - X[k] * math.sqrt(math.log(2) / mu)) < 1e-12
+
+
+def test_whitening_constant_power_and_scale_invariance():
+    nb = 500
+    ph = np.exp(1j * np.linspace(0, 40, nb))
+    Xw = O.whiten(3.0 * ph)
+    assert np.allclose(np.abs(Xw[1:]) ** 2, math.log(2), rtol=1e-13)
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal(nb) + 1j * rng.standard_normal(nb)
+    assert np.allclose(O.whiten(7.5 * X), O.whiten(X), rtol=1e-12, atol=1e-14)
+
+
+def test_whitening_rejects_short_spectrum():
+    with pytest.raises(ValueError):
+        O.whiten(np.ones(64, dtype=complex))
+
+
+# ------------------------------------------------------- harmonic sums --
+def test_subharmonic_rounding_rules():
+    # round half up in r
+    assert list(O.subharmonic_r([0, 1, 2, 3, 5, 7], 1, 2)) == [0, 1, 1, 2, 3, 4]
+    assert list(O.subharmonic_r([8, 9, 10], 3, 4)) == [6, 7, 8]
+    # ties away from zero in the centred z index, symmetric about zc
+    zc = 10
+    assert list(O.subharmonic_j([9, 11, 7, 13], 1, 2, zc)) == [9, 11, 8, 12]
+    assert list(O.subharmonic_j([10], 5, 16, zc)) == [10]
+
+
+def test_harmonic_sum_invariants():
+    Z, nb = 21, 200
+    zc = 10
+    # constant plane: H_h = h c
+    H = O.harmonic_sums(np.full((Z, nb), 2.5), 16)
+    for h, v in H.items():
+        assert np.allclose(v, 2.5 * h)
+    # plane = column index: at r = h t, H_h = sum_k k t = t h (h+1) / 2
+    P = np.tile(np.arange(nb, dtype=float), (Z, 1))
+    H = O.harmonic_sums(P, 16)
+    for h in (1, 2, 4, 8, 16):
+        for t in (1, 3, 12):
+            r = h * t
+            if r < nb:
+                assert H[h][4, r] == t * h * (h + 1) / 2
+    # plane = centred row index: at jc = h t, H_h = sum_k k t
+    P = np.tile((np.arange(Z) - zc)[:, None].astype(float), (1, nb))
+    H = O.harmonic_sums(P, 8)
+    for h in (1, 2, 4, 8):
+        for t in (-1, 1):
+            j = zc + h * t
+            if 0 <= j < Z:
+                assert H[h][j, 50] == t * h * (h + 1) / 2
+    # z-mirror symmetry of the plane carries over to the sums
+    rng = np.random.default_rng(0)
+    half = rng.random((zc + 1, nb))
+    P = np.vstack([half[:0:-1], half])
+    H = O.harmonic_sums(P, 16)
+    for v in H.values():
+        assert np.allclose(v, v[::-1])
+
+
+def test_harmonic_sum_brute_force_hot_cell():
+    """A single unit cell at (j0, r0) appears in H_h exactly at the top cells
+    whose k-th sub-harmonic lands on it; counted here by brute force."""
+    Z, nb = 17, 120
+    zc = 8
+    j0, r0 = 9, 7
+    P = np.zeros((Z, nb))
+    P[j0, r0] = 1.0
+    H = O.harmonic_sums(P, 16)
+    for h in (1, 2, 4, 8, 16):
+        for j in range(Z):
+            for r in range(nb):
+                cnt = 0
+                for k in range(1, h + 1):
+                    rr = math.floor(k * r / h + 0.5)
+                    jc = j - zc
+                    x = k * jc / h
+                    jj = zc + int(math.copysign(math.floor(abs(x) + 0.5), x))
+                    cnt += (rr == r0 and jj == j0)
+                assert H[h][j, r] == cnt
+    assert H[2][zc + 2 * (j0 - zc), 2 * r0] >= 1
+
+
+# ------------------------------------------------------------- thresholds --
+def test_thresholds_closed_forms():
+    p = O.gaussian_tail(6.0)
+    assert abs(p - 9.865876450377e-10) < 1e-20
+    T = O.thresholds(16, 6.0)
+    assert abs(T[1] + math.log(p)) < 1e-10           # Gamma(1) is exponential
+    for h, t in T.items():
+        # Poisson form of the upper tail of Gamma(h, 1) for integer h
+        q = math.exp(-t) * sum(t ** i / math.factorial(i) for i in range(h))
+        assert abs(q / p - 1.0) < 1e-9
+
+
+def test_threshold_false_alarm_rate_monte_carlo():
+    """At 2 sigma the false-alarm rate of sums of h unit exponentials at T_h
+    matches the Gaussian tail (so the thresholds have the right meaning)."""
+    rng = np.random.default_rng(7)
+    T = O.thresholds(16, 2.0)
+    p = O.gaussian_tail(2.0)
+    for h, t in T.items():
+        s = rng.exponential(size=(400000, h)).sum(axis=1)
+        rate = np.mean(s >= t)
+        assert abs(rate - p) < 5 * math.sqrt(p / 400000)
+
+
+def test_thresholds_golden_table():
+    with open(os.path.join(GOLDEN, "thresholds_sigma6.json")) as f:
+        g = json.load(f)
+    T = O.thresholds(16, 6.0)
+    for h, v in g["T"].items():
+        assert abs(T[int(h)] - v) < 1e-9
