@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Throughput of the FDAS path on the SKA-shaped single-trial workload:
+N = 2^23 float32 samples (Gaussian noise + 20 accelerated sinusoids with up
+to 8 harmonics), zmax = 200, dz = 2 (201 templates of 512 taps), segments of
+8192 bins, float32 power plane, harmonic sums 1..16, 6-sigma threshold.
+
+One step = one DM trial through the whole path (real FFT, whitening, segment
+FFTs, fused correlation, harmonic sum, threshold, compaction) with the series
+already resident in HBM; `e2e` repeats the measurement through the C ABI with
+host buffers (host->device copy of the series and device->host copy of the
+candidate list inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU: one process per GPU (torchrun); DM trials are independent, so
+every rank processes its own trials with no data-path collective (weak
+scaling); the timed region is bracketed by barriers and the max over ranks
+is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "cfg2_n2e23_z200"
+METRIC = "DM trials/s at N=2^23 zmax=200"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return dict(PEAKS_FALLBACK, sm_max_mhz=2070.0), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.file is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = []
+        for i, n in enumerate(names):
+            if any(r[5 + i].lower().startswith("active") for r in rows):
+                reasons.append(n)
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle, timed on a bounded sample of one trial.
+# ---------------------------------------------------------------------------
+def oracle_trial_estimate(x, p, rows=3, hs_width=1 << 15):
+    """Seconds per trial of the oracle, from a bounded sample: the spectrum
+    and whitening of the full series, `rows` of the 201 plane rows, and the
+    harmonic sums over `hs_width` of the 2^22 top bins (all 201 rows); the
+    per-row and per-bin costs are scaled to the whole trial."""
+    from oracle import fdas_oracle as O
+    t0 = time.perf_counter()
+    Xw = O.whiten(O.spectrum(x))
+    t_pre = time.perf_counter() - t0
+    zs = O.z_values(p["zmax"], p["dz"])
+    Z = len(zs)
+    t0 = time.perf_counter()
+    for z in zs[:: max(1, Z // rows)][:rows]:
+        tau = O.template_fresnel(float(z), p["m"])
+        O.correlate_row(Xw, tau)
+    t_row = (time.perf_counter() - t0) / rows
+    rng = np.random.default_rng(0)
+    Psub = rng.exponential(size=(Z, hs_width))
+    t0 = time.perf_counter()
+    H = O.harmonic_sums(Psub, p["nharm"])
+    T = O.thresholds(p["nharm"], p["sigma"])
+    for h, v in H.items():
+        np.nonzero(v >= T[h])
+    t_hs = (time.perf_counter() - t0) * (x.shape[0] // 2) / hs_width
+    total = t_pre + Z * t_row + t_hs
+    sample = (f"oracle on 1 host core: full spectrum+whitening, {rows} of {Z} plane rows, "
+              f"harmonic sums over {hs_width} of {x.shape[0] // 2} bins; scaled to one trial "
+              f"({os.cpu_count()} host cores present)")
+    return total, sample
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is 1/Z of a trial (one
+    plane row, 1/Z of the harmonic sums and of the spectrum+whitening)."""
+    from oracle import fdas_oracle as O
+    from synthetic import workload
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    x, p = workload(WORKLOAD)
+    zs = O.z_values(p["zmax"], p["dz"])
+    Z = len(zs)
+    t0 = time.perf_counter()
+    Xw = O.whiten(O.spectrum(x))
+    t_pre = (time.perf_counter() - t0) / Z
+    rng = np.random.default_rng(0)
+    width = max(1, (x.shape[0] // 2) // Z)
+    Psub = rng.exponential(size=(Z, width))
+    T = O.thresholds(p["nharm"], p["sigma"])
+
+    def step(i):
+        tau = O.template_fresnel(float(zs[i % Z]), p["m"])
+        O.correlate_row(Xw, tau)
+        H = O.harmonic_sums(Psub, p["nharm"])
+        for h, v in H.items():
+            np.nonzero(v >= T[h])
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(i)
+    dt = (time.perf_counter() - t0) / args.steps + t_pre
+    value = 1.0 / (Z * dt)
+    sample = (f"each step = 1/{Z} of a trial on 1 host core (one plane row, harmonic sums over "
+              f"{width} bins x {Z} rows, 1/{Z} of spectrum+whitening)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "trials/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": p["N"], "zmax": p["zmax"], "dz": p["dz"],
+                       "templates": Z, "template_width": p["m"], "segment": p["L"],
+                       "nharm": p["nharm"], "sigma": p["sigma"]},
+            "cpu_baseline": {"value": value, "unit": "trials/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "trials/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--series", type=int, default=4, help="distinct resident series cycled")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1511_07343_gb300 import fdas
+    from synthetic import workload
+
+    x0, p = workload(WORKLOAD, seed=2 + 1000 * rank, device=dev)
+    series = [x0] + [workload(WORKLOAD, seed=3 + i + 1000 * rank, device=dev)[0]
+                     for i in range(args.series - 1)]
+    d_series = [torch.from_numpy(s).to(dev) for s in series]
+
+    stream = torch.cuda.Stream(dev)
+    max_cands = 1 << 22
+    plan = fdas.fdas_plan_create(p["N"], p["zmax"], p["dz"], p["m"], p["L"], p["nharm"],
+                                 p["sigma"], max_cands, stream.cuda_stream)
+    info = fdas.fdas_plan_get_info(plan)
+    d_out = torch.empty(max_cands * 16, dtype=torch.uint8, device=dev)
+    d_cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def step(i):
+        fdas.fdas_search_device(plan, d_series[i % len(d_series)], 1, d_out, d_cnt)
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            step(i)
+    torch.cuda.synchronize(dev)
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for i in range(args.steps):
+            step(i)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+    ms_per_step = ms / args.steps
+    value = args.steps * world / (ms / 1e3)
+    n_cands = int(d_cnt.item())
+
+    # per-stage times (CUDA events inside the library, same stream)
+    stages = ["spectrum", "whiten", "segments", "correlate", "harmsum"]
+    prof = np.stack([fdas.fdas_profile_trial(plan, d_series[i % len(d_series)])
+                     for i in range(3)])
+    stage_ms = {s: float(np.median(prof[:, i])) for i, s in enumerate(stages)}
+
+    # end to end through the C ABI with host buffers
+    e2e_steps = args.e2e_steps or max(3, min(args.steps, 10))
+    h_series = torch.from_numpy(series[0]).pin_memory()
+    h_out = np.zeros(max_cands, dtype=fdas.CAND_DTYPE)
+    h_cnt = np.zeros(1, dtype=np.int64)
+    fdas.fdas_search_host(plan, h_series.data_ptr(), 1, h_out, h_cnt)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    d2h = 0
+    for i in range(e2e_steps):
+        fdas.fdas_search_host(plan, h_series.data_ptr(), 1, h_out, h_cnt)
+        d2h += 8 + 16 * int(min(h_cnt[0], max_cands))
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    fdas.fdas_plan_destroy(plan)
+
+    peaks, peak_kind = load_peaks()
+    # dominant kernel and its roofline
+    dom = max(stage_ms, key=stage_ms.get)
+    N, Z, L, m, V, S, nb = p["N"], info.Z, info.L, info.m, info.V, info.S, info.nb
+    if dom == "correlate":
+        flops = S * Z * (5.0 * L * math.log2(L) + 6.0 * L + 3.0 * V)
+        sm_max = peaks.get("sm_max_mhz", 2070.0)
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        achieved = flops / (stage_ms[dom] / 1e3) / 1e12
+        roof = {"kernel": "k_correlate", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                               f"{sm_max:.0f} MHz",
+                "algorithmic": f"S*Z*(5 L log2 L + 6 L + 3 V) = {flops:.3e} flop per launch",
+                "hbm_view_gbs": (Z * nb * 4) / (stage_ms[dom] / 1e3) / 1e9}
+    else:
+        nbytes = Z * nb * 4.0
+        peak = peaks["hbm_gbs"]
+        achieved = nbytes / (stage_ms[dom] / 1e3) / 1e9
+        roof = {"kernel": "k_harmsum" if dom == "harmsum" else dom, "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic": f"one read of the Z x nb float32 plane = {nbytes:.3e} B per launch"}
+
+    line = {"metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "zmax": p["zmax"], "dz": p["dz"],
+                       "templates": Z, "template_width": m, "segment": L, "nharm": p["nharm"],
+                       "sigma": p["sigma"], "parallelism": f"replicas{world}",
+                       "l2": f"{len(d_series)} resident series cycled; each step writes a "
+                             f"{Z * nb * 4 / 1e9:.2f} GB plane (> L2)"},
+            "stage_ms": stage_ms, "candidates_last_step": n_cands,
+            "roofline": roof,
+            "clocks": clocks,
+            "e2e": {"value": 1.0 / e2e_s, "unit": "trials/s", "h2d_bytes_per_step": 4 * N,
+                    "d2h_bytes_per_step": int(d2h / e2e_steps)},
+            "gpu_launches": int(info_kernels_per_trial() * args.steps),
+            "peaks": {"source": peak_kind, "hbm_gbs": peaks.get("hbm_gbs")}}
+    if rank == 0 and not args.no_cpu_baseline:
+        t_trial, sample = oracle_trial_estimate(series[0], p)
+        line["cpu_baseline"] = {"value": 1.0 / t_trial, "unit": "trials/s", "cores": 1,
+                                "kind": "oracle", "sample": sample}
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def info_kernels_per_trial():
+    # real FFT (columns, rows, unpack), whitening, segment FFTs, correlation,
+    # harmonic sum
+    return 7
+
+
+if __name__ == "__main__":
+    sys.exit(main())

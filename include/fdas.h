@@ -1,0 +1,150 @@
+/*
+ * fdas.h - C ABI of the GB300 (sm_103a) Fourier Domain Acceleration Search.
+ *
+ * The library implements the hot path of the FDAS method of Dimoudi &
+ * Armour, "Pulsar Acceleration Searches on the GPU for the Square Kilometre
+ * Array" (Sections 2 and 4): for each de-dispersed time series
+ *   real FFT (step 2) -> 64-bin running-median whitening ->
+ *   overlapped segments (step 3) -> segment FFT (step 4) ->
+ *   multiply by the conjugated z-templates (step 5) -> inverse FFT (step 6) ->
+ *   power and edge removal (step 7) = the f-fdot power plane of Eq. 1 ->
+ *   harmonic sums h = 1, 2, 4, 8, 16 -> threshold -> compacted candidate list.
+ *
+ * Conventions (all entry points):
+ *  - Every function returns an int status: FDAS_OK (0) or a negative
+ *    FDAS_ERR_* code; nothing throws across the ABI. fdas_strerror() maps a
+ *    code to text, fdas_last_error() gives the detail of the last failure on
+ *    the calling thread.
+ *  - Pointers named d_* are device pointers, h_* host pointers. The caller
+ *    owns every buffer it passes; the plan owns everything it allocates on
+ *    the device (templates, twiddle tables, workspaces) and frees it in
+ *    fdas_plan_destroy().
+ *  - A plan is bound to the CUDA stream given at creation (NULL = the legacy
+ *    default stream) and is not thread-safe; use one plan per stream.
+ *  - Complex data are interleaved float32 (re, im) pairs, i.e. float2.
+ *
+ * Notation: N samples per series, nb = N/2 Fourier bins (Nyquist dropped),
+ * z_j = -zmax + j*dz for j = 0..Z-1 (Z = 2*zmax/dz + 1, z = fdot*T^2 in bins,
+ * Section 2), m template taps, L segment length, V = L - m valid outputs per
+ * segment, S = ceil(nb / V) segments.
+ */
+#ifndef FDAS_H
+#define FDAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum fdas_status {
+  FDAS_OK = 0,
+  FDAS_ERR_INVALID = -1,  /* bad argument or unsupported size */
+  FDAS_ERR_NOMEM = -2,    /* a device or host allocation failed */
+  FDAS_ERR_CUDA = -3,     /* a CUDA runtime call or kernel launch failed */
+  FDAS_ERR_TIMEOUT = -4,  /* a bounded device wait gave up */
+  FDAS_ERR_OVERFLOW = -5  /* more candidates than max_cands (count still exact) */
+};
+
+typedef struct fdas_plan fdas_plan;
+
+/* One detection: the harmonic sum H_h at top-harmonic bin r_top and template
+ * index z_idx (z = -zmax + z_idx*dz) reached the threshold T_h. */
+typedef struct {
+  int32_t r_top;
+  int32_t z_idx;
+  int32_t h;
+  float power;
+} fdas_cand;
+
+typedef struct {
+  int64_t N, nb;
+  int32_t zmax, dz, Z, m, L, V, S, nharm, n_levels;
+  float thresholds[5];      /* T_h for h = 1, 2, 4, 8, 16 (first n_levels used) */
+  int64_t max_cands;
+  int64_t device_bytes;     /* device memory the plan holds */
+  int64_t plane_floats;     /* Z * nb */
+} fdas_plan_info;
+
+/* Creates a plan: validates sizes, allocates the device workspaces and runs
+ * the initialisation stage of Section 4 (template computation): the Fresnel
+ * response tau_z(d) of Section 2 for d = -m/2..m/2-1 in float64 on the GPU,
+ * its length-L spectrum (float64 DFT, scaled by 1/L and rounded to float32),
+ * and the float64-generated FFT twiddle tables.
+ *   N: power of two, 2^12 <= N <= 2^24.  zmax >= 0, dz > 0, dz | zmax.
+ *   template_width m: even, 8 <= m.  segment L: 2048, 4096 or 8192, L >= 2m.
+ *   nharm: 1, 2, 4, 8 or 16.  sigma > 0: Gaussian-equivalent threshold.
+ *   max_cands >= 1: capacity of the candidate list per trial.
+ *   stream: a cudaStream_t (may be NULL).
+ * On error *out is NULL and nothing is leaked. */
+int fdas_plan_create(fdas_plan** out, int64_t N, int32_t zmax, int32_t dz,
+                     int32_t template_width, int32_t segment, int32_t nharm,
+                     float sigma, int64_t max_cands, void* stream);
+
+int fdas_plan_destroy(fdas_plan* plan);
+
+int fdas_plan_get_info(const fdas_plan* plan, fdas_plan_info* info);
+
+/* The full path (Section 4 steps 2-7, harmonic sum, threshold, compaction)
+ * on n_trials series stored back to back at d_series (N floats each, device).
+ * Candidates of trial t go to h_out + t*max_cands (host, caller-owned),
+ * sorted by (h, r_top, z_idx); h_counts[t] is the exact number found, which
+ * may exceed max_cands: then only max_cands are stored and the call returns
+ * FDAS_ERR_OVERFLOW after finishing every trial. Synchronises the stream. */
+int fdas_search(fdas_plan* plan, const float* d_series, int32_t n_trials,
+                fdas_cand* h_out, int64_t* h_counts);
+
+/* As fdas_search, but the series are in host memory (step 1 of Section 4:
+ * the transfer to the GPU is part of the call; page-locked memory makes it
+ * asynchronous). */
+int fdas_search_host(fdas_plan* plan, const float* h_series, int32_t n_trials,
+                     fdas_cand* h_out, int64_t* h_counts);
+
+/* Device-resident variant: enqueues the whole path on the plan's stream and
+ * returns without synchronising. Candidates of trial t go, unsorted, to
+ * d_out + t*max_cands and d_counts[t] (device int64) receives the exact count
+ * (entries past max_cands are dropped). */
+int fdas_search_device(fdas_plan* plan, const float* d_series, int32_t n_trials,
+                       fdas_cand* d_out, int64_t* d_counts);
+
+/* Test hook: copies the float32 power plane of the last trial processed,
+ * Z x nb row-major by z (P[j*nb + r] = |A(r, z_j)|^2, Eq. 1), to d_plane. */
+int fdas_plane_debug(fdas_plan* plan, float* d_plane);
+
+/* Stage entry points (device pointers, asynchronous on the plan's stream),
+ * used by the per-stage parity tests. */
+/* Step 2: X_k = sum_n x_n exp(-2 pi i k n/N), k = 0..nb-1 -> d_spectrum (nb float2). */
+int fdas_stage_spectrum(fdas_plan* plan, const float* d_series, float* d_spectrum);
+/* Whitening: mu_k = median of |X|^2 over the 64-bin window [k-32, k+31]
+ * shifted into [1, nb-1]; Xw_k = X_k sqrt(ln2/mu_k), Xw_0 = 0 (nb float2). */
+int fdas_stage_whiten(fdas_plan* plan, const float* d_spectrum, float* d_white);
+/* Steps 3-7 on a whitened spectrum: writes the Z x nb float32 plane. */
+int fdas_stage_plane(fdas_plan* plan, const float* d_white, float* d_plane);
+/* Harmonic sum + threshold + compaction on a caller-supplied Z x nb plane;
+ * d_count: one device int64. */
+int fdas_stage_harmsum(fdas_plan* plan, const float* d_plane, fdas_cand* d_out,
+                       int64_t* d_count);
+/* Template taps tau_{z_j}(d), float64 complex, Z x m (d = -m/2..m/2-1). */
+int fdas_template_taps(fdas_plan* plan, double* d_taps);
+/* Template spectra (1/L) sum_d tau(d) exp(+2 pi i k d/L), float2, Z x L. */
+int fdas_template_bank(fdas_plan* plan, float* d_bank);
+
+/* Per-stage timing of one trial on the plan's stream (CUDA events around
+ * each kernel launch group; synchronises). h_ms[0..4] receive milliseconds
+ * for: spectrum (step 2), whitening, segment FFTs (steps 3-4), correlation
+ * (steps 5-7), harmonic sum + threshold + compaction. */
+int fdas_profile_trial(fdas_plan* plan, const float* d_series, float* h_ms);
+
+/* Host-side Fresnel integrals C(x), S(x) of the library's own float64
+ * implementation (the one the template kernel runs), for CPU checks. */
+int fdas_host_fresnel(double x, double* C, double* S);
+
+const char* fdas_strerror(int status);
+const char* fdas_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDAS_H */

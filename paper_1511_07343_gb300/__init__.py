@@ -1,0 +1,7 @@
+"""GB300-native (sm_103a) Fourier Domain Acceleration Search.
+
+The compute path lives in the CUDA library ``_build/libfdas_gb300.so``
+(sources in ``csrc/``, C ABI in ``include/fdas.h``); ``fdas`` is its ctypes
+binding and ``search`` a small convenience layer over it.
+"""
+from . import fdas  # noqa: F401

@@ -1,0 +1,391 @@
+// C ABI of the FDAS library: plan lifetime, the search entry points and the
+// per-stage hooks. Host logic only; every arithmetic step of the path runs in
+// the kernels of the other translation units.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "fdas_internal.h"
+
+namespace fdas {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return FDAS_OK;
+  return set_error(e == cudaErrorMemoryAllocation ? FDAS_ERR_NOMEM : FDAS_ERR_CUDA,
+                   std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+namespace {
+
+bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+int log2i(int64_t x) {
+  int l = 0;
+  while ((int64_t(1) << l) < x) ++l;
+  return l;
+}
+
+// Upper tail of Gamma(h, 1) for integer h: Q(h, x) = exp(-x) sum_{i<h} x^i / i!.
+double gamma_q_int(int h, double x) {
+  double term = 1.0, sum = 1.0;
+  for (int i = 1; i < h; ++i) {
+    term *= x / i;
+    sum += term;
+  }
+  return exp(-x) * sum;
+}
+
+// T with Q(h, T) = p: bisection on log Q (monotone), then Newton polish.
+double gamma_q_inv_int(int h, double p) {
+  double lo = 0.0, hi = 1.0;
+  while (gamma_q_int(h, hi) > p) hi *= 2.0;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (gamma_q_int(h, mid) > p) lo = mid; else hi = mid;
+  }
+  double x = 0.5 * (lo + hi);
+  for (int it = 0; it < 3; ++it) {
+    double lf = 1.0;
+    for (int i = 1; i < h; ++i) lf *= i;
+    const double dq = -exp(-x) * pow(x, h - 1) / lf;  // dQ/dx
+    const double f = log(gamma_q_int(h, x)) - log(p);
+    const double df = dq / gamma_q_int(h, x);
+    if (df != 0.0) x -= f / df;
+  }
+  return x;
+}
+
+template <typename T>
+int dalloc(fdas_plan* p, T** ptr, size_t count) {
+  const size_t bytes = count * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    return set_error(FDAS_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                         cudaGetErrorString(e));
+  }
+  p->device_bytes += (int64_t)bytes;
+  return FDAS_OK;
+}
+
+void free_plan(fdas_plan* p) {
+  if (!p) return;
+  void* ptrs[] = {p->tw_L, p->tw_M1, p->tw_M2, p->tw4_lo, p->tw4_hi, p->twN_lo, p->twN_hi,
+                  p->taps, p->bank, p->series, p->zbuf, p->spec, p->spec2, p->white, p->seg,
+                  p->plane, p->cands, p->count};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete p;
+}
+
+// The path for one trial; the plane goes to p->plane, candidates to d_out.
+int run_trial(fdas_plan* p, const float* d_x, fdas_cand* d_out, unsigned long long* d_count) {
+  int rc;
+  if ((rc = cuda_check(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), p->stream),
+                       "memset count")))
+    return rc;
+  if ((rc = launch_spectrum(p, d_x, p->spec))) return rc;
+  if ((rc = launch_whiten(p, p->spec, p->white))) return rc;
+  if ((rc = launch_segments(p, p->white))) return rc;
+  if ((rc = launch_correlate(p, p->plane))) return rc;
+  return launch_harmsum(p, p->plane, d_out, d_count);
+}
+
+bool cand_less(const fdas_cand& a, const fdas_cand& b) {
+  if (a.h != b.h) return a.h < b.h;
+  if (a.r_top != b.r_top) return a.r_top < b.r_top;
+  return a.z_idx < b.z_idx;
+}
+
+int search_impl(fdas_plan* p, const float* d_series, int32_t n_trials, fdas_cand* h_out,
+                int64_t* h_counts) {
+  bool overflow = false;
+  for (int32_t t = 0; t < n_trials; ++t) {
+    int rc = run_trial(p, d_series + (size_t)t * p->N, p->cands, p->count);
+    if (rc) return rc;
+    unsigned long long cnt = 0;
+    rc = cuda_check(cudaMemcpyAsync(&cnt, p->count, sizeof(cnt), cudaMemcpyDeviceToHost,
+                                    p->stream),
+                    "copy count");
+    if (rc) return rc;
+    if ((rc = cuda_check(cudaStreamSynchronize(p->stream), "sync count"))) return rc;
+    h_counts[t] = (int64_t)cnt;
+    const int64_t keep = std::min<int64_t>((int64_t)cnt, p->max_cands);
+    if ((int64_t)cnt > p->max_cands) overflow = true;
+    fdas_cand* dst = h_out + (size_t)t * p->max_cands;
+    if (keep > 0) {
+      rc = cuda_check(cudaMemcpyAsync(dst, p->cands, sizeof(fdas_cand) * keep,
+                                      cudaMemcpyDeviceToHost, p->stream),
+                      "copy candidates");
+      if (rc) return rc;
+      if ((rc = cuda_check(cudaStreamSynchronize(p->stream), "sync candidates"))) return rc;
+      std::sort(dst, dst + keep, cand_less);
+    }
+  }
+  return overflow ? set_error(FDAS_ERR_OVERFLOW, "candidate list overflow") : FDAS_OK;
+}
+
+}  // namespace
+}  // namespace fdas
+
+using namespace fdas;
+
+extern "C" {
+
+int fdas_plan_create(fdas_plan** out, int64_t N, int32_t zmax, int32_t dz, int32_t m,
+                     int32_t L, int32_t nharm, float sigma, int64_t max_cands, void* stream) {
+  if (!out) return set_error(FDAS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!is_pow2(N) || N < (1 << 12) || N > (1 << 24))
+    return set_error(FDAS_ERR_INVALID, "N must be a power of two in [2^12, 2^24]");
+  if (zmax < 0 || dz <= 0 || zmax % dz != 0)
+    return set_error(FDAS_ERR_INVALID, "need zmax >= 0, dz > 0 and dz | zmax");
+  if (m < 8 || (m & 1)) return set_error(FDAS_ERR_INVALID, "template width must be even, >= 8");
+  if (L != 2048 && L != 4096 && L != 8192)
+    return set_error(FDAS_ERR_INVALID, "segment length must be 2048, 4096 or 8192");
+  if (L < 2 * m) return set_error(FDAS_ERR_INVALID, "segment length must be >= 2 * width");
+  if (nharm != 1 && nharm != 2 && nharm != 4 && nharm != 8 && nharm != 16)
+    return set_error(FDAS_ERR_INVALID, "nharm must be 1, 2, 4, 8 or 16");
+  if (!(sigma > 0.f)) return set_error(FDAS_ERR_INVALID, "sigma must be > 0");
+  if (max_cands < 1) return set_error(FDAS_ERR_INVALID, "max_cands must be >= 1");
+  if ((int64_t)(2 * (zmax / dz) + 1) * (N / 2) > (int64_t(1) << 40))
+    return set_error(FDAS_ERR_INVALID, "plane too large");
+
+  fdas_plan* p = new fdas_plan();
+  p->N = N;
+  p->nb = N / 2;
+  p->M = N / 2;
+  const int h = log2i(p->M);
+  p->M1 = 1 << ((h + 1) / 2);
+  p->M2 = 1 << (h / 2);
+  p->zmax = zmax;
+  p->dz = dz;
+  p->Z = 2 * (zmax / dz) + 1;
+  p->m = m;
+  p->L = L;
+  p->V = L - m;
+  p->S = (int)((p->nb + p->V - 1) / p->V);
+  p->nharm = nharm;
+  p->n_levels = log2i(nharm) + 1;
+  p->sigma = sigma;
+  p->max_cands = max_cands;
+  p->stream = (cudaStream_t)stream;
+  const double ptail = 0.5 * erfc((double)sigma / sqrt(2.0));
+  for (int i = 0; i < p->n_levels; ++i) p->thr[i] = (float)gamma_q_inv_int(1 << i, ptail);
+  p->h4 = (h + 1) / 2;
+  p->hN = (h + 1) / 2;
+
+  int rc = FDAS_OK;
+#define TRY(x)            \
+  do {                    \
+    if ((rc = (x))) {     \
+      free_plan(p);       \
+      return rc;          \
+    }                     \
+  } while (0)
+  TRY(dalloc(p, &p->tw_L, L));
+  TRY(dalloc(p, &p->tw_M1, p->M1));
+  TRY(dalloc(p, &p->tw_M2, p->M2));
+  TRY(dalloc(p, &p->tw4_lo, (size_t)1 << p->h4));
+  TRY(dalloc(p, &p->tw4_hi, (size_t)(p->M >> p->h4) + 1));
+  TRY(dalloc(p, &p->twN_lo, (size_t)1 << p->hN));
+  TRY(dalloc(p, &p->twN_hi, (size_t)(p->M >> p->hN) + 1));
+  TRY(dalloc(p, &p->taps, (size_t)p->Z * m));
+  TRY(dalloc(p, &p->bank, (size_t)p->Z * L));
+  TRY(dalloc(p, &p->series, (size_t)N));
+  TRY(dalloc(p, &p->zbuf, (size_t)p->M));
+  TRY(dalloc(p, &p->spec, (size_t)p->nb));
+  TRY(dalloc(p, &p->spec2, (size_t)p->M));
+  TRY(dalloc(p, &p->white, (size_t)p->nb));
+  TRY(dalloc(p, &p->seg, (size_t)p->S * L));
+  TRY(dalloc(p, &p->plane, (size_t)p->Z * p->nb));
+  TRY(dalloc(p, &p->cands, (size_t)max_cands));
+  TRY(dalloc(p, &p->count, 1));
+
+  cudaStream_t s = p->stream;
+  TRY(launch_twiddles(p->tw_L, L, 1, L, s));
+  TRY(launch_twiddles(p->tw_M1, p->M1, 1, p->M1, s));
+  TRY(launch_twiddles(p->tw_M2, p->M2, 1, p->M2, s));
+  TRY(launch_twiddles(p->tw4_lo, (int64_t)1 << p->h4, 1, p->M, s));
+  TRY(launch_twiddles(p->tw4_hi, (p->M >> p->h4) + 1, (int64_t)1 << p->h4, p->M, s));
+  TRY(launch_twiddles(p->twN_lo, (int64_t)1 << p->hN, 1, p->N, s));
+  TRY(launch_twiddles(p->twN_hi, (p->M >> p->hN) + 1, (int64_t)1 << p->hN, p->N, s));
+  TRY(launch_template_taps(p));
+  TRY(launch_template_bank(p));
+  TRY(cuda_check(cudaStreamSynchronize(s), "plan initialisation"));
+#undef TRY
+  *out = p;
+  return FDAS_OK;
+}
+
+int fdas_plan_destroy(fdas_plan* p) {
+  if (!p) return FDAS_OK;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  free_plan(p);
+  return FDAS_OK;
+}
+
+int fdas_plan_get_info(const fdas_plan* p, fdas_plan_info* info) {
+  if (!p || !info) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  memset(info, 0, sizeof(*info));
+  info->N = p->N;
+  info->nb = p->nb;
+  info->zmax = p->zmax;
+  info->dz = p->dz;
+  info->Z = p->Z;
+  info->m = p->m;
+  info->L = p->L;
+  info->V = p->V;
+  info->S = p->S;
+  info->nharm = p->nharm;
+  info->n_levels = p->n_levels;
+  for (int i = 0; i < 5; ++i) info->thresholds[i] = p->thr[i];
+  info->max_cands = p->max_cands;
+  info->device_bytes = p->device_bytes;
+  info->plane_floats = (int64_t)p->Z * p->nb;
+  return FDAS_OK;
+}
+
+int fdas_search(fdas_plan* p, const float* d_series, int32_t n_trials, fdas_cand* h_out,
+                int64_t* h_counts) {
+  if (!p || !d_series || n_trials < 0 || (n_trials > 0 && (!h_out || !h_counts)))
+    return set_error(FDAS_ERR_INVALID, "bad argument to fdas_search");
+  return search_impl(p, d_series, n_trials, h_out, h_counts);
+}
+
+int fdas_search_host(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_cand* h_out,
+                     int64_t* h_counts) {
+  if (!p || !h_series || n_trials < 0 || (n_trials > 0 && (!h_out || !h_counts)))
+    return set_error(FDAS_ERR_INVALID, "bad argument to fdas_search_host");
+  bool overflow = false;
+  for (int32_t t = 0; t < n_trials; ++t) {
+    int rc = cuda_check(cudaMemcpyAsync(p->series, h_series + (size_t)t * p->N,
+                                        sizeof(float) * p->N, cudaMemcpyHostToDevice, p->stream),
+                        "copy series");
+    if (rc) return rc;
+    rc = search_impl(p, p->series, 1, h_out + (size_t)t * p->max_cands, h_counts + t);
+    if (rc == FDAS_ERR_OVERFLOW) overflow = true;
+    else if (rc) return rc;
+  }
+  return overflow ? set_error(FDAS_ERR_OVERFLOW, "candidate list overflow") : FDAS_OK;
+}
+
+int fdas_search_device(fdas_plan* p, const float* d_series, int32_t n_trials, fdas_cand* d_out,
+                       int64_t* d_counts) {
+  if (!p || !d_series || n_trials < 0 || (n_trials > 0 && (!d_out || !d_counts)))
+    return set_error(FDAS_ERR_INVALID, "bad argument to fdas_search_device");
+  for (int32_t t = 0; t < n_trials; ++t) {
+    int rc = run_trial(p, d_series + (size_t)t * p->N, d_out + (size_t)t * p->max_cands,
+                       reinterpret_cast<unsigned long long*>(d_counts + t));
+    if (rc) return rc;
+  }
+  return FDAS_OK;
+}
+
+int fdas_plane_debug(fdas_plan* p, float* d_plane) {
+  if (!p || !d_plane) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  return cuda_check(cudaMemcpyAsync(d_plane, p->plane, sizeof(float) * (size_t)p->Z * p->nb,
+                                    cudaMemcpyDeviceToDevice, p->stream),
+                    "copy plane");
+}
+
+int fdas_stage_spectrum(fdas_plan* p, const float* d_series, float* d_spectrum) {
+  if (!p || !d_series || !d_spectrum) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  return launch_spectrum(p, d_series, reinterpret_cast<float2*>(d_spectrum));
+}
+
+int fdas_stage_whiten(fdas_plan* p, const float* d_spectrum, float* d_white) {
+  if (!p || !d_spectrum || !d_white) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  return launch_whiten(p, reinterpret_cast<const float2*>(d_spectrum),
+                       reinterpret_cast<float2*>(d_white));
+}
+
+int fdas_stage_plane(fdas_plan* p, const float* d_white, float* d_plane) {
+  if (!p || !d_white || !d_plane) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  int rc = launch_segments(p, reinterpret_cast<const float2*>(d_white));
+  if (rc) return rc;
+  return launch_correlate(p, d_plane);
+}
+
+int fdas_stage_harmsum(fdas_plan* p, const float* d_plane, fdas_cand* d_out, int64_t* d_count) {
+  if (!p || !d_plane || !d_out || !d_count) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  int rc = cuda_check(cudaMemsetAsync(d_count, 0, sizeof(int64_t), p->stream), "memset count");
+  if (rc) return rc;
+  return launch_harmsum(p, d_plane, d_out, reinterpret_cast<unsigned long long*>(d_count));
+}
+
+int fdas_template_taps(fdas_plan* p, double* d_taps) {
+  if (!p || !d_taps) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  return cuda_check(cudaMemcpyAsync(d_taps, p->taps, sizeof(double2) * (size_t)p->Z * p->m,
+                                    cudaMemcpyDeviceToDevice, p->stream),
+                    "copy taps");
+}
+
+int fdas_template_bank(fdas_plan* p, float* d_bank) {
+  if (!p || !d_bank) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  return cuda_check(cudaMemcpyAsync(d_bank, p->bank, sizeof(float2) * (size_t)p->Z * p->L,
+                                    cudaMemcpyDeviceToDevice, p->stream),
+                    "copy bank");
+}
+
+int fdas_profile_trial(fdas_plan* p, const float* d_series, float* h_ms) {
+  if (!p || !d_series || !h_ms) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  cudaEvent_t ev[6];
+  for (int i = 0; i < 6; ++i) {
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+      for (int k = 0; k < i; ++k) cudaEventDestroy(ev[k]);
+      return set_error(FDAS_ERR_CUDA, "cudaEventCreate failed");
+    }
+  }
+  int rc = cuda_check(cudaMemsetAsync(p->count, 0, sizeof(unsigned long long), p->stream),
+                      "memset count");
+  if (!rc) rc = cuda_check(cudaEventRecord(ev[0], p->stream), "event");
+  if (!rc) rc = launch_spectrum(p, d_series, p->spec);
+  if (!rc) rc = cuda_check(cudaEventRecord(ev[1], p->stream), "event");
+  if (!rc) rc = launch_whiten(p, p->spec, p->white);
+  if (!rc) rc = cuda_check(cudaEventRecord(ev[2], p->stream), "event");
+  if (!rc) rc = launch_segments(p, p->white);
+  if (!rc) rc = cuda_check(cudaEventRecord(ev[3], p->stream), "event");
+  if (!rc) rc = launch_correlate(p, p->plane);
+  if (!rc) rc = cuda_check(cudaEventRecord(ev[4], p->stream), "event");
+  if (!rc) rc = launch_harmsum(p, p->plane, p->cands, p->count);
+  if (!rc) rc = cuda_check(cudaEventRecord(ev[5], p->stream), "event");
+  if (!rc) rc = cuda_check(cudaEventSynchronize(ev[5]), "event sync");
+  for (int i = 0; i < 5 && !rc; ++i)
+    rc = cuda_check(cudaEventElapsedTime(&h_ms[i], ev[i], ev[i + 1]), "elapsed");
+  for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+  return rc;
+}
+
+int fdas_host_fresnel(double x, double* C, double* S) {
+  if (!C || !S) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  fresnel_host(x, C, S);
+  return FDAS_OK;
+}
+
+const char* fdas_strerror(int status) {
+  switch (status) {
+    case FDAS_OK: return "ok";
+    case FDAS_ERR_INVALID: return "invalid argument";
+    case FDAS_ERR_NOMEM: return "out of memory";
+    case FDAS_ERR_CUDA: return "CUDA error";
+    case FDAS_ERR_TIMEOUT: return "device wait timed out";
+    case FDAS_ERR_OVERFLOW: return "candidate list overflow";
+  }
+  return "unknown status";
+}
+
+const char* fdas_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

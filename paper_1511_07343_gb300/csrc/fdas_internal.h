@@ -1,0 +1,75 @@
+// Internal plan layout and kernel launchers of the FDAS CUDA path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/fdas.h"
+
+struct fdas_plan {
+  // sizes
+  int64_t N = 0, nb = 0, M = 0;  // M = N/2 complex points of the packed real FFT
+  int M1 = 0, M2 = 0;            // four-step split M = M1 * M2
+  int zmax = 0, dz = 0, Z = 0, m = 0, L = 0, V = 0, S = 0;
+  int nharm = 0, n_levels = 0;
+  float sigma = 6.f;
+  float thr[5] = {0, 0, 0, 0, 0};
+  int64_t max_cands = 0;
+  cudaStream_t stream = nullptr;
+
+  // tables (float64-made)
+  float2* tw_L = nullptr;      // exp(-2 pi i e / L), e < L
+  float2* tw_M1 = nullptr;     // exp(-2 pi i e / M1)
+  float2* tw_M2 = nullptr;     // exp(-2 pi i e / M2)
+  float2* tw4_lo = nullptr;    // four-step twiddle exp(-2 pi i e / M), e < 2^h4
+  float2* tw4_hi = nullptr;    //   exp(-2 pi i (e << h4) / M)
+  int h4 = 0;
+  float2* twN_lo = nullptr;    // real-FFT unpack twiddle exp(-2 pi i k / N), k < 2^hN
+  float2* twN_hi = nullptr;
+  int hN = 0;
+
+  // templates
+  double2* taps = nullptr;     // Z x m float64 taps
+  float2* bank = nullptr;      // Z x L spectra, 1/L folded in
+
+  // per-trial workspaces
+  float* series = nullptr;     // N floats (host-input staging)
+  float2* zbuf = nullptr;      // M complex (four-step scratch)
+  float2* spec = nullptr;      // nb complex spectrum
+  float2* spec2 = nullptr;     // M complex packed FFT (before the real-FFT unpack)
+  float2* white = nullptr;     // nb complex whitened spectrum
+  float2* seg = nullptr;       // S x L segment spectra
+  float* plane = nullptr;      // Z x nb power plane
+  fdas_cand* cands = nullptr;  // max_cands
+  unsigned long long* count = nullptr;
+
+  int64_t device_bytes = 0;
+};
+
+namespace fdas {
+
+// error plumbing
+int set_error(int code, const std::string& msg);
+int cuda_check(cudaError_t e, const char* what);
+
+// fdas_templates.cu
+int launch_twiddles(float2* out, int64_t count, int64_t mult, int64_t period, cudaStream_t s);
+int launch_template_taps(fdas_plan* p);
+int launch_template_bank(fdas_plan* p);
+void fresnel_host(double x, double* C, double* S);
+
+// fdas_spectrum.cu
+int launch_spectrum(fdas_plan* p, const float* d_series, float2* d_spec);
+int launch_whiten(fdas_plan* p, const float2* d_spec, float2* d_white);
+
+// fdas_correlate.cu
+int launch_segments(fdas_plan* p, const float2* d_white);
+int launch_correlate(fdas_plan* p, float* d_plane);
+
+// fdas_harmsum.cu
+int launch_harmsum(fdas_plan* p, const float* d_plane, fdas_cand* d_out,
+                   unsigned long long* d_count);
+
+}  // namespace fdas

@@ -1,0 +1,86 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every
+symbol the header declares, validates arguments before touching the GPU, and
+its float64 Fresnel integrals (the ones the template kernel runs) agree with
+scipy's."""
+import os
+import re
+
+import numpy as np
+import pytest
+from scipy import special
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1511_07343_gb300 import build as b
+    b.build()
+    from paper_1511_07343_gb300 import fdas
+    fdas.load()
+    return fdas
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^[A-Za-z_][\w\s\*]*?\b(fdas_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("fdas_plan_create", "fdas_plan_destroy", "fdas_search", "fdas_plane_debug",
+                     "fdas_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import ctypes
+    so = ctypes.CDLL(lib.library_path())
+    missing = [n for n in declared_functions() if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_binding_uses_header_names(lib):
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+
+
+@pytest.mark.parametrize("x", list(np.linspace(-30, 30, 241)) + [1.79, 1.8, 1.81, 1e-3, 250.3, -410.7])
+def test_host_fresnel_matches_scipy(lib, x):
+    c, s = lib.fdas_host_fresnel(float(x))
+    S, C = special.fresnel(x)
+    assert abs(c - C) < 2e-14 and abs(s - S) < 2e-14, (x, c - C, s - S)
+
+
+@pytest.mark.parametrize("args", [
+    dict(N=3000), dict(N=1 << 11), dict(N=1 << 25), dict(zmax=-2), dict(dz=0), dict(zmax=5, dz=2),
+    dict(m=7), dict(m=4), dict(L=1024), dict(L=2048, m=1100), dict(nharm=3), dict(nharm=32),
+    dict(sigma=0.0), dict(max_cands=0)])
+def test_plan_create_rejects_bad_arguments(lib, args):
+    p = dict(N=1 << 14, zmax=20, dz=2, m=64, L=2048, nharm=4, sigma=6.0, max_cands=100)
+    p.update(args)
+    with pytest.raises(lib.FdasError) as e:
+        lib.fdas_plan_create(p["N"], p["zmax"], p["dz"], p["m"], p["L"], p["nharm"], p["sigma"],
+                             p["max_cands"])
+    assert e.value.status == lib.FDAS_ERR_INVALID
+
+
+def test_strerror(lib):
+    assert lib.fdas_strerror(0) == "ok"
+    assert "overflow" in lib.fdas_strerror(lib.FDAS_ERR_OVERFLOW)
+    assert lib.fdas_strerror(-99) == "unknown status"
+
+
+def test_null_arguments_are_rejected(lib):
+    import ctypes
+    so = lib.load()
+    assert so.fdas_search(None, None, 1, None, None) == lib.FDAS_ERR_INVALID
+    assert so.fdas_plan_destroy(None) == lib.FDAS_OK
+    assert so.fdas_plan_get_info(None, None) == lib.FDAS_ERR_INVALID
+    assert so.fdas_host_fresnel(1.0, None, None) == lib.FDAS_ERR_INVALID
+    del ctypes
