@@ -203,6 +203,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--series", type=int, default=4, help="distinct resident series cycled")
+    ap.add_argument("--log2n", type=int, default=None,
+                    help="smaller series length for profiling captures (not a bench value)")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -224,9 +227,17 @@ def main():
     from paper_1511_07343_gb300 import fdas
     from synthetic import workload
 
-    x0, p = workload(WORKLOAD, seed=2 + 1000 * rank, device=dev)
-    series = [x0] + [workload(WORKLOAD, seed=3 + i + 1000 * rank, device=dev)[0]
-                     for i in range(args.series - 1)]
+    if args.log2n is not None:
+        from synthetic import WORKLOADS, make_series, random_chirps
+        p = dict(WORKLOADS[WORKLOAD])
+        p["N"] = 1 << args.log2n
+        rng = np.random.default_rng(11)
+        series = [make_series(p["N"], 20 + i, random_chirps(rng, 20, p["N"], p["zmax"]),
+                              device=dev) for i in range(args.series)]
+    else:
+        x0, p = workload(WORKLOAD, seed=2 + 1000 * rank, device=dev)
+        series = [x0] + [workload(WORKLOAD, seed=3 + i + 1000 * rank, device=dev)[0]
+                         for i in range(args.series - 1)]
     d_series = [torch.from_numpy(s).to(dev) for s in series]
 
     stream = torch.cuda.Stream(dev)
@@ -275,18 +286,19 @@ def main():
     stage_ms = {s: float(np.median(prof[:, i])) for i, s in enumerate(stages)}
 
     # end to end through the C ABI with host buffers
-    e2e_steps = args.e2e_steps or max(3, min(args.steps, 10))
+    e2e_steps = 0 if args.no_e2e else (args.e2e_steps or max(3, min(args.steps, 10)))
     h_series = torch.from_numpy(series[0]).pin_memory()
     h_out = np.zeros(max_cands, dtype=fdas.CAND_DTYPE)
     h_cnt = np.zeros(1, dtype=np.int64)
-    fdas.fdas_search_host(plan, h_series.data_ptr(), 1, h_out, h_cnt)
+    if e2e_steps:
+        fdas.fdas_search_host(plan, h_series.data_ptr(), 1, h_out, h_cnt)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     d2h = 0
     for i in range(e2e_steps):
         fdas.fdas_search_host(plan, h_series.data_ptr(), 1, h_out, h_cnt)
         d2h += 8 + 16 * int(min(h_cnt[0], max_cands))
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = (time.perf_counter() - t0) / max(e2e_steps, 1)
     fdas.fdas_plan_destroy(plan)
 
     peaks, peak_kind = load_peaks()
@@ -325,8 +337,9 @@ def main():
             "stage_ms": stage_ms, "candidates_last_step": n_cands,
             "roofline": roof,
             "clocks": clocks,
-            "e2e": {"value": 1.0 / e2e_s, "unit": "trials/s", "h2d_bytes_per_step": 4 * N,
-                    "d2h_bytes_per_step": int(d2h / e2e_steps)},
+            "e2e": {"value": 1.0 / e2e_s if e2e_steps else None, "unit": "trials/s",
+                    "h2d_bytes_per_step": 4 * N,
+                    "d2h_bytes_per_step": int(d2h / max(e2e_steps, 1))},
             "gpu_launches": int(info_kernels_per_trial() * args.steps),
             "peaks": {"source": peak_kind, "hbm_gbs": peaks.get("hbm_gbs")}}
     if rank == 0 and not args.no_cpu_baseline:

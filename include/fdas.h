@@ -65,6 +65,8 @@ typedef struct {
   int64_t max_cands;
   int64_t device_bytes;     /* device memory the plan holds */
   int64_t plane_floats;     /* Z * nb */
+  int32_t corr_ctas_per_sm; /* launch shape of the correlation kernel (0 before the first search) */
+  int32_t corr_grid;
 } fdas_plan_info;
 
 /* Creates a plan: validates sizes, allocates the device workspaces and runs
@@ -73,7 +75,7 @@ typedef struct {
  * its length-L spectrum (float64 DFT, scaled by 1/L and rounded to float32),
  * and the float64-generated FFT twiddle tables.
  *   N: power of two, 2^12 <= N <= 2^24.  zmax >= 0, dz > 0, dz | zmax.
- *   template_width m: even, 8 <= m.  segment L: 2048, 4096 or 8192, L >= 2m.
+ *   template_width m: multiple of 8, m >= 8.  segment L: 2048, 4096 or 8192, L >= 2m.
  *   nharm: 1, 2, 4, 8 or 16.  sigma > 0: Gaussian-equivalent threshold.
  *   max_cands >= 1: capacity of the candidate list per trial.
  *   stream: a cudaStream_t (may be NULL).

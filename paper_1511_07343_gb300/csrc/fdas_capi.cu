@@ -83,7 +83,7 @@ void free_plan(fdas_plan* p) {
   if (!p) return;
   void* ptrs[] = {p->tw_L, p->tw_M1, p->tw_M2, p->tw4_lo, p->tw4_hi, p->twN_lo, p->twN_hi,
                   p->taps, p->bank, p->series, p->zbuf, p->spec, p->spec2, p->white, p->seg,
-                  p->plane, p->cands, p->count};
+                  p->plane, p->q4, p->cands, p->count};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -98,8 +98,8 @@ int run_trial(fdas_plan* p, const float* d_x, fdas_cand* d_out, unsigned long lo
   if ((rc = launch_spectrum(p, d_x, p->spec))) return rc;
   if ((rc = launch_whiten(p, p->spec, p->white))) return rc;
   if ((rc = launch_segments(p, p->white))) return rc;
-  if ((rc = launch_correlate(p, p->plane))) return rc;
-  return launch_harmsum(p, p->plane, d_out, d_count);
+  if ((rc = launch_correlate(p, p->plane, p->q4, d_out, d_count))) return rc;
+  return launch_harmsum(p, p->plane, p->q4, d_out, d_count);
 }
 
 bool cand_less(const fdas_cand& a, const fdas_cand& b) {
@@ -151,7 +151,7 @@ int fdas_plan_create(fdas_plan** out, int64_t N, int32_t zmax, int32_t dz, int32
     return set_error(FDAS_ERR_INVALID, "N must be a power of two in [2^12, 2^24]");
   if (zmax < 0 || dz <= 0 || zmax % dz != 0)
     return set_error(FDAS_ERR_INVALID, "need zmax >= 0, dz > 0 and dz | zmax");
-  if (m < 8 || (m & 1)) return set_error(FDAS_ERR_INVALID, "template width must be even, >= 8");
+  if (m < 8 || (m & 7)) return set_error(FDAS_ERR_INVALID, "template width must be a multiple of 8");
   if (L != 2048 && L != 4096 && L != 8192)
     return set_error(FDAS_ERR_INVALID, "segment length must be 2048, 4096 or 8192");
   if (L < 2 * m) return set_error(FDAS_ERR_INVALID, "segment length must be >= 2 * width");
@@ -210,6 +210,7 @@ int fdas_plan_create(fdas_plan** out, int64_t N, int32_t zmax, int32_t dz, int32
   TRY(dalloc(p, &p->white, (size_t)p->nb));
   TRY(dalloc(p, &p->seg, (size_t)p->S * L));
   TRY(dalloc(p, &p->plane, (size_t)p->Z * p->nb));
+  TRY(dalloc(p, &p->q4, (size_t)p->Z * (p->nb / 4)));
   TRY(dalloc(p, &p->cands, (size_t)max_cands));
   TRY(dalloc(p, &p->count, 1));
 
@@ -254,6 +255,8 @@ int fdas_plan_get_info(const fdas_plan* p, fdas_plan_info* info) {
   info->max_cands = p->max_cands;
   info->device_bytes = p->device_bytes;
   info->plane_floats = (int64_t)p->Z * p->nb;
+  info->corr_ctas_per_sm = p->corr_ctas_per_sm;
+  info->corr_grid = p->corr_grid;
   return FDAS_OK;
 }
 
@@ -315,14 +318,16 @@ int fdas_stage_plane(fdas_plan* p, const float* d_white, float* d_plane) {
   if (!p || !d_white || !d_plane) return set_error(FDAS_ERR_INVALID, "NULL argument");
   int rc = launch_segments(p, reinterpret_cast<const float2*>(d_white));
   if (rc) return rc;
-  return launch_correlate(p, d_plane);
+  return launch_correlate(p, d_plane, nullptr, nullptr, nullptr);
 }
 
 int fdas_stage_harmsum(fdas_plan* p, const float* d_plane, fdas_cand* d_out, int64_t* d_count) {
   if (!p || !d_plane || !d_out || !d_count) return set_error(FDAS_ERR_INVALID, "NULL argument");
   int rc = cuda_check(cudaMemsetAsync(d_count, 0, sizeof(int64_t), p->stream), "memset count");
   if (rc) return rc;
-  return launch_harmsum(p, d_plane, d_out, reinterpret_cast<unsigned long long*>(d_count));
+  auto* cnt = reinterpret_cast<unsigned long long*>(d_count);
+  if ((rc = launch_pool4(p, d_plane, p->q4, d_out, cnt))) return rc;
+  return launch_harmsum(p, d_plane, p->q4, d_out, cnt);
 }
 
 int fdas_template_taps(fdas_plan* p, double* d_taps) {
@@ -357,9 +362,9 @@ int fdas_profile_trial(fdas_plan* p, const float* d_series, float* h_ms) {
   if (!rc) rc = cuda_check(cudaEventRecord(ev[2], p->stream), "event");
   if (!rc) rc = launch_segments(p, p->white);
   if (!rc) rc = cuda_check(cudaEventRecord(ev[3], p->stream), "event");
-  if (!rc) rc = launch_correlate(p, p->plane);
+  if (!rc) rc = launch_correlate(p, p->plane, p->q4, p->cands, p->count);
   if (!rc) rc = cuda_check(cudaEventRecord(ev[4], p->stream), "event");
-  if (!rc) rc = launch_harmsum(p, p->plane, p->cands, p->count);
+  if (!rc) rc = launch_harmsum(p, p->plane, p->q4, p->cands, p->count);
   if (!rc) rc = cuda_check(cudaEventRecord(ev[5], p->stream), "event");
   if (!rc) rc = cuda_check(cudaEventSynchronize(ev[5]), "event sync");
   for (int i = 0; i < 5 && !rc; ++i)

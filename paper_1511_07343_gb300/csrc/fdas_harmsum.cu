@@ -12,6 +12,7 @@
 //     H_1 = t16, H_2 = H_1 + t8, H_4 = H_2 + (t4 + t12),
 //     H_8 = H_4 + ((t2 + t6) + (t10 + t14)), H_16 = H_8 + (odd q terms).
 #include "fdas_common.cuh"
+#include "fdas_emit.cuh"
 #include "fdas_internal.h"
 
 namespace fdas {
@@ -21,74 +22,224 @@ struct Thr {
   float t[5];
 };
 
-__device__ __forceinline__ void emit(bool pred, int r, int j, int h, float H, fdas_cand* out,
-                                     unsigned long long* count, int64_t maxc) {
-  const unsigned mask = __ballot_sync(0xffffffffu, pred);
-  if (mask == 0) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(mask) - 1;
-  unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(mask));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (pred) {
-    const unsigned long long slot = base + __popc(mask & ((1u << lane) - 1u));
-    if (slot < (unsigned long long)maxc) {
-      fdas_cand c;
-      c.r_top = r;
-      c.z_idx = j;
-      c.h = h;
-      c.power = H;
-      out[slot] = c;
+// Q4[j][g] = max(P[j][4g .. 4g+3]) and the h = 1 candidates of a given plane
+// (the correlation kernel produces both itself; this serves planes supplied
+// from outside).
+__global__ void __launch_bounds__(256) k_pool4(const float* __restrict__ P, float* __restrict__ Q4,
+                                               int64_t nb, float thr1, fdas_cand* __restrict__ out,
+                                               unsigned long long* count, int64_t maxc) {
+  const int j = blockIdx.y;
+  const int64_t nq = nb >> 2;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool gv = g < nq;
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (gv) {
+    v = __ldg(reinterpret_cast<const float4*>(P + (size_t)j * nb) + g);
+    Q4[(size_t)j * nq + g] = fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w));
+  }
+  const int r0 = (int)(4 * g);
+  emit(gv && r0 >= 1 && v.x >= thr1, r0, j, 1, v.x, out, count, maxc);
+  emit(gv && v.y >= thr1, r0 + 1, j, 1, v.y, out, count, maxc);
+  emit(gv && v.z >= thr1, r0 + 2, j, 1, v.z, out, count, maxc);
+  emit(gv && v.w >= thr1, r0 + 3, j, 1, v.w, out, count, maxc);
+}
+
+// Harmonic sums h >= 2, screened, in a fixed summation order: the fractions
+// q/16 are added one after the other as q = 16, 8 | 4, 12 | 2, 6, 10, 14 |
+// 1, 3, .., 15, so H_2, H_4, H_8 and H_16 are the running sums after 2, 4, 8
+// and 16 terms. A block takes top row j and 16384 consecutive top bins
+// R0 .. R0 + 16383 (R0 a multiple of 16384); thread t owns the 64 bins
+// R0 + 64 t + i. For fraction q the sub-harmonic bin is
+//     rr = round(q r / 16) = q R0/16 + 4 q t + K(q, i),  K(q, i) = (2 q i + 16) >> 5,
+// so its 4-bin group is q R0/64 + q t + (K(q, i) >> 2): a compile-time offset
+// from q t once the block's slice of row jz(q) of Q4 is staged in shared
+// memory (coalesced loads, one entry per word, padded against bank
+// conflicts). Every term is bounded by its group maximum and each pair of
+// adjacent bins shares one bound (the larger of its two groups); float
+// addition is monotone, so a pair whose running bound stays below T_h cannot
+// hold a candidate at level h. The rare flagged pairs are summed exactly from
+// P in the same order and compared with T_h.
+__host__ __device__ constexpr int frac_order(int i) {
+  return i == 0 ? 16 : i == 1 ? 8 : i == 2 ? 4 : i == 3 ? 12 : i < 8 ? 2 + 4 * (i - 4)
+                                                                     : 1 + 2 * (i - 8);
+}
+__host__ __device__ constexpr int kq(int q, int i) { return (2 * q * i + 16) >> 5; }
+__device__ __forceinline__ int spad(int e) { return e + (e >> 5); }
+
+constexpr int kHsThreads = 256;
+constexpr int kHsCells = 64;
+constexpr int kHsSpan = kHsThreads * kHsCells;
+constexpr int kStageN = 16 * kHsThreads + 1;            // entries staged for q = 16
+constexpr int kStageW = kStageN + (kStageN >> 5) + 1;   // padded words
+constexpr size_t kHsSmem = 3 * kStageW * sizeof(float);
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src),
+               "r"(ok ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait1() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+template <int NLEV>
+__global__ void __launch_bounds__(kHsThreads) k_harmsum_staged(
+    const float* __restrict__ P, const float* __restrict__ Q4, int64_t nb, int Z, Thr thr,
+    fdas_cand* __restrict__ out, unsigned long long* count, int64_t maxc) {
+  constexpr int NQ = 1 << (NLEV - 1);
+  extern __shared__ float stage[];  // 3 x kStageW, rotating
+  const int j = blockIdx.y;
+  const int64_t R0 = (int64_t)blockIdx.x * kHsSpan;
+  const int tid = threadIdx.x;
+  const int64_t nq = nb >> 2;
+  const int zc = (Z - 1) / 2;
+  const int jc = j - zc;
+  const int ajc = jc < 0 ? -jc : jc;
+  const int sg = jc < 0 ? -1 : 1;
+  // asynchronous copy of the block's slice of row jz(q) of Q4 (fraction
+  // number oi in summation order) into rotating buffer oi % 3
+  auto issue = [&](int oi) {
+    if (oi < NQ) {
+      const int q = frac_order(oi);
+      float* sb = stage + (oi % 3) * kStageW;
+      const int row = zc + sg * ((2 * q * ajc + 16) >> 5);
+      const int64_t e_lo = (int64_t)q * (R0 >> 6);
+      const int cnt = kHsThreads * q + 1;
+      const float* src = Q4 + (size_t)row * nq + e_lo;
+      for (int e = tid; e < cnt; e += kHsThreads) {
+        const bool ok = e_lo + e < nq;
+        cp_async4(sb + spad(e), ok ? src + e : Q4, ok);
+      }
+    }
+    cp_async_commit();
+  };
+  float acc[kHsCells / 2];
+  unsigned pmask = 0;
+  issue(0);
+  issue(1);
+#pragma unroll
+  for (int oi = 0; oi < NQ; ++oi) {
+    const int q = frac_order(oi);
+    cp_async_wait1();
+    __syncthreads();
+    issue(oi + 2);
+    const float* sb = stage + (oi % 3) * kStageW;
+    const int base = q * tid;
+#pragma unroll
+    for (int pr = 0; pr < kHsCells / 2; ++pr) {
+      const int o1 = kq(q, 2 * pr) >> 2;
+      const int o2 = kq(q, 2 * pr + 1) >> 2;
+      float v = sb[spad(base + o1)];
+      if (o2 != o1) v = fmaxf(v, sb[spad(base + o2)]);
+      acc[pr] = (oi == 0) ? v : acc[pr] + v;
+    }
+    if (oi == 1 || oi == 3 || oi == 7 || oi == 15) {
+      const int lvl = oi == 1 ? 1 : (oi == 3 ? 2 : (oi == 7 ? 3 : 4));
+      const float t = thr.t[lvl];
+      float mx = acc[0];
+#pragma unroll
+      for (int pr = 1; pr < kHsCells / 2; ++pr) mx = fmaxf(mx, acc[pr]);
+      if (mx >= t) {
+#pragma unroll
+        for (int pr = 0; pr < kHsCells / 2; ++pr)
+          if (acc[pr] >= t) pmask |= 1u << pr;
+      }
+    }
+  }
+  // pairs past the end of the spectrum
+  const int64_t first = R0 + (int64_t)kHsCells * tid;
+  if (first >= nb) pmask = 0;
+  else if (first + kHsCells > nb) pmask &= (1u << ((nb - first) >> 1)) - 1u;
+  // exact sums of the flagged pairs, same order as the bound
+  while (pmask) {
+    const int pr = __ffs(pmask) - 1;
+    pmask &= pmask - 1;
+    for (int c = 0; c < 2; ++c) {
+      const int64_t r64 = first + 2 * pr + c;
+      if (r64 < 1 || r64 >= nb) continue;
+      const int r = (int)r64;
+      float H = 0.f;
+#pragma unroll
+      for (int oi = 0; oi < NQ; ++oi) {
+        const int q = frac_order(oi);
+        const int jzq = zc + sg * ((2 * q * ajc + 16) >> 5);
+        const float v = __ldg(P + (size_t)jzq * nb + ((2 * q * r + 16) >> 5));
+        H = (oi == 0) ? v : H + v;
+        if (oi == 1 || oi == 3 || oi == 7 || oi == 15) {
+          const int lvl = oi == 1 ? 1 : (oi == 3 ? 2 : (oi == 7 ? 3 : 4));
+          if (H >= thr.t[lvl]) {
+            const unsigned long long slot = atomicAdd(count, 1ull);
+            if (slot < (unsigned long long)maxc) {
+              fdas_cand cd;
+              cd.r_top = r;
+              cd.z_idx = j;
+              cd.h = 1 << lvl;
+              cd.power = H;
+              out[slot] = cd;
+            }
+          }
+        }
+      }
     }
   }
 }
 
-// Direct form: one thread per top cell, the 16 fraction terms gathered from
-// the plane (sub-harmonic rows and columns are re-read through L1/L2).
-__global__ void __launch_bounds__(256) k_harmsum_direct(const float* __restrict__ P, int64_t nb,
-                                                        int Z, int n_levels, Thr thr,
-                                                        fdas_cand* __restrict__ out,
-                                                        unsigned long long* count, int64_t maxc) {
-  const int j = blockIdx.y;
-  const int64_t r64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = r64 >= 1 && r64 < nb;
-  const int r = valid ? (int)r64 : 1;
-  const int zc = (Z - 1) / 2;
-  const int jc = j - zc;
-  const int sg = jc < 0 ? -1 : 1;
-  auto term = [&](int q) -> float {
-    const int rr = (2 * q * r + 16) >> 5;
-    const int a = q * (jc < 0 ? -jc : jc);
-    const int jz = zc + sg * ((2 * a + 16) >> 5);
-    return __ldg(P + (size_t)jz * nb + rr);
-  };
-  float H = term(16);
-  emit(valid && H >= thr.t[0], r, j, 1, H, out, count, maxc);
-  if (n_levels < 2) return;
-  H = H + term(8);
-  emit(valid && H >= thr.t[1], r, j, 2, H, out, count, maxc);
-  if (n_levels < 3) return;
-  H = H + (term(4) + term(12));
-  emit(valid && H >= thr.t[2], r, j, 4, H, out, count, maxc);
-  if (n_levels < 4) return;
-  H = H + ((term(2) + term(6)) + (term(10) + term(14)));
-  emit(valid && H >= thr.t[3], r, j, 8, H, out, count, maxc);
-  if (n_levels < 5) return;
-  H = H + (((term(1) + term(3)) + (term(5) + term(7))) +
-           ((term(9) + term(11)) + (term(13) + term(15))));
-  emit(valid && H >= thr.t[4], r, j, 16, H, out, count, maxc);
+Thr thresholds_of(const fdas_plan* p) {
+  Thr thr;
+  for (int i = 0; i < 5; ++i) thr.t[i] = p->thr[i];
+  return thr;
 }
 
 }  // namespace
 
-int launch_harmsum(fdas_plan* p, const float* d_plane, fdas_cand* d_out,
+int launch_pool4(fdas_plan* p, const float* d_plane, float* d_q4, fdas_cand* d_out,
+                 unsigned long long* d_count) {
+  const int64_t nq = p->nb >> 2;
+  dim3 grid((unsigned)((nq + 255) / 256), p->Z);
+  k_pool4<<<grid, 256, 0, p->stream>>>(d_plane, d_q4, p->nb, p->thr[0], d_out, d_count,
+                                       p->max_cands);
+  return cuda_check(cudaGetLastError(), "k_pool4");
+}
+
+int launch_harmsum(fdas_plan* p, const float* d_plane, const float* d_q4, fdas_cand* d_out,
                    unsigned long long* d_count) {
-  Thr thr;
-  for (int i = 0; i < 5; ++i) thr.t[i] = p->thr[i];
-  dim3 grid((unsigned)((p->nb + 255) / 256), p->Z);
-  k_harmsum_direct<<<grid, 256, 0, p->stream>>>(d_plane, p->nb, p->Z, p->n_levels, thr, d_out,
-                                                d_count, p->max_cands);
-  return cuda_check(cudaGetLastError(), "k_harmsum_direct");
+  if (p->n_levels < 2) return FDAS_OK;
+  dim3 grid((unsigned)((p->nb + kHsSpan - 1) / kHsSpan), p->Z);
+  const Thr thr = thresholds_of(p);
+  static bool attr_set[6] = {false, false, false, false, false, false};
+  if (!attr_set[p->n_levels]) {
+    cudaError_t e = cudaSuccess;
+    switch (p->n_levels) {
+      case 2: e = cudaFuncSetAttribute(k_harmsum_staged<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHsSmem); break;
+      case 3: e = cudaFuncSetAttribute(k_harmsum_staged<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHsSmem); break;
+      case 4: e = cudaFuncSetAttribute(k_harmsum_staged<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHsSmem); break;
+      default: e = cudaFuncSetAttribute(k_harmsum_staged<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHsSmem); break;
+    }
+    if (e != cudaSuccess) return cuda_check(e, "k_harmsum_staged attr");
+    attr_set[p->n_levels] = true;
+  }
+  switch (p->n_levels) {
+    case 2:
+      k_harmsum_staged<2><<<grid, kHsThreads, kHsSmem, p->stream>>>(d_plane, d_q4, p->nb, p->Z, thr,
+                                                            d_out, d_count, p->max_cands);
+      break;
+    case 3:
+      k_harmsum_staged<3><<<grid, kHsThreads, kHsSmem, p->stream>>>(d_plane, d_q4, p->nb, p->Z, thr,
+                                                            d_out, d_count, p->max_cands);
+      break;
+    case 4:
+      k_harmsum_staged<4><<<grid, kHsThreads, kHsSmem, p->stream>>>(d_plane, d_q4, p->nb, p->Z, thr,
+                                                            d_out, d_count, p->max_cands);
+      break;
+    default:
+      k_harmsum_staged<5><<<grid, kHsThreads, kHsSmem, p->stream>>>(d_plane, d_q4, p->nb, p->Z, thr,
+                                                            d_out, d_count, p->max_cands);
+  }
+  return cuda_check(cudaGetLastError(), "k_harmsum_staged");
 }
 
 }  // namespace fdas

@@ -42,10 +42,13 @@ struct fdas_plan {
   float2* white = nullptr;     // nb complex whitened spectrum
   float2* seg = nullptr;       // S x L segment spectra
   float* plane = nullptr;      // Z x nb power plane
+  float* q4 = nullptr;         // Z x nb/4 maxima of 4 consecutive plane bins
   fdas_cand* cands = nullptr;  // max_cands
   unsigned long long* count = nullptr;
 
   int64_t device_bytes = 0;
+  int corr_ctas_per_sm = 0;  // launch shape of the correlation kernel (last launch)
+  int corr_grid = 0;
 };
 
 namespace fdas {
@@ -66,10 +69,13 @@ int launch_whiten(fdas_plan* p, const float2* d_spec, float2* d_white);
 
 // fdas_correlate.cu
 int launch_segments(fdas_plan* p, const float2* d_white);
-int launch_correlate(fdas_plan* p, float* d_plane);
+int launch_correlate(fdas_plan* p, float* d_plane, float* d_q4, fdas_cand* d_cands,
+                     unsigned long long* d_count);
 
 // fdas_harmsum.cu
-int launch_harmsum(fdas_plan* p, const float* d_plane, fdas_cand* d_out,
+int launch_pool4(fdas_plan* p, const float* d_plane, float* d_q4, fdas_cand* d_out,
+                 unsigned long long* d_count);
+int launch_harmsum(fdas_plan* p, const float* d_plane, const float* d_q4, fdas_cand* d_out,
                    unsigned long long* d_count);
 
 }  // namespace fdas

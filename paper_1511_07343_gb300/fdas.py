@@ -34,7 +34,8 @@ class fdas_plan_info(ctypes.Structure):
                 ("m", ctypes.c_int32), ("L", ctypes.c_int32), ("V", ctypes.c_int32),
                 ("S", ctypes.c_int32), ("nharm", ctypes.c_int32), ("n_levels", ctypes.c_int32),
                 ("thresholds", ctypes.c_float * 5), ("max_cands", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64), ("plane_floats", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("plane_floats", ctypes.c_int64),
+                ("corr_ctas_per_sm", ctypes.c_int32), ("corr_grid", ctypes.c_int32)]
 
 
 CAND_DTYPE = np.dtype([("r_top", "<i4"), ("z_idx", "<i4"), ("h", "<i4"), ("power", "<f4")])
