@@ -339,9 +339,7 @@ int fdas_template_taps(fdas_plan* p, double* d_taps) {
 
 int fdas_template_bank(fdas_plan* p, float* d_bank) {
   if (!p || !d_bank) return set_error(FDAS_ERR_INVALID, "NULL argument");
-  return cuda_check(cudaMemcpyAsync(d_bank, p->bank, sizeof(float2) * (size_t)p->Z * p->L,
-                                    cudaMemcpyDeviceToDevice, p->stream),
-                    "copy bank");
+  return launch_bank_natural(p, reinterpret_cast<float2*>(d_bank));
 }
 
 int fdas_profile_trial(fdas_plan* p, const float* d_series, float* h_ms) {

@@ -1,5 +1,6 @@
 // Shared device building blocks of the FDAS CUDA path: complex helpers,
-// in-register radix-R DFTs and a shared-memory Stockham FFT.
+// in-register radix-R DFTs (scalar and packed-pair) and a shared-memory
+// Stockham FFT.
 //
 // All FFTs here compute y_k = sum_j x_j exp(DIR * 2 pi i j k / R) with
 // DIR = -1 (forward) or +1 (inverse, unnormalised). Twiddle tables are
@@ -156,6 +157,122 @@ FDAS_DEV void stockham_from(float2* buf, const float2* __restrict__ tw, int tid)
 template <int L, int DIR, int NT, int NB>
 FDAS_DEV void block_fft(float2* buf, const float2* __restrict__ tw, int tid) {
   stockham_from<L, 1, DIR, NT, NB>(buf, tw, tid);
+}
+
+}  // namespace fdas
+
+// ---------------------------------------------------------------------------
+// Paired complex arithmetic on packed f32x2 (sm_100 family): a c2 holds two
+// independent complex values, (re0, re1) and (im0, im1), so one packed
+// instruction advances two transforms at once.
+// ---------------------------------------------------------------------------
+namespace fdas {
+
+struct c2 {
+  float2 re, im;
+};
+
+FDAS_DEV float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+FDAS_DEV float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+FDAS_DEV float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+FDAS_DEV float2 p_sub(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+      "mov.b64 pa, {%2, %3};\n\t"
+      "mov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pd, pa, pb;\n\t"
+      "mov.b64 {%0, %1}, pd;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+FDAS_DEV float2 p_neg(float2 a) { return p_mul(a, make_float2(-1.f, -1.f)); }
+
+FDAS_DEV c2 c2_add(c2 a, c2 b) { return c2{p_add(a.re, b.re), p_add(a.im, b.im)}; }
+FDAS_DEV c2 c2_sub(c2 a, c2 b) { return c2{p_sub(a.re, b.re), p_sub(a.im, b.im)}; }
+// a * b, both data
+FDAS_DEV c2 c2_mul(c2 a, c2 b) {
+  return c2{p_sub(p_mul(a.re, b.re), p_mul(a.im, b.im)), p_fma(a.re, b.im, p_mul(a.im, b.re))};
+}
+// a * (C + i S) with per-lane cosines C and sines S
+FDAS_DEV c2 c2_mul_cs(c2 a, float2 C, float2 S) {
+  return c2{p_sub(p_mul(a.re, C), p_mul(a.im, S)), p_fma(a.re, S, p_mul(a.im, C))};
+}
+
+// exp(DIR 2 pi i e / R) applied lane-wise, lane 0 exponent e0, lane 1 e1
+// (compile-time after unrolling, 0 <= e < R, R | 32).
+template <int DIR>
+FDAS_DEV c2 c2_rot(c2 v, int e0, int e1, int R) {
+  const int k0 = e0 * (32 / R), k1 = e1 * (32 / R);
+  if (k0 == 0 && k1 == 0) return v;
+  if (k0 == 8 && k1 == 8)  // times DIR * i
+    return DIR < 0 ? c2{v.im, p_neg(v.re)} : c2{p_neg(v.im), v.re};
+  auto cs = [](int k, float& c, float& s) {
+    // cos, sin of 2 pi k / 32 for 0 <= k < 32
+    const int kk = k & 15;
+    c = kCos32[kk];
+    s = kSin32[kk];
+    if (k >= 16) {
+      c = -c;
+      s = -s;
+    }
+  };
+  float c0, s0, c1, s1;
+  cs(k0, c0, s0);
+  cs(k1, c1, s1);
+  if (DIR < 0) {
+    s0 = -s0;
+    s1 = -s1;
+  }
+  return c2_mul_cs(v, make_float2(c0, c1), make_float2(s0, s1));
+}
+
+// In-register radix-R DFT of two independent lanes (radix-2 decimation in
+// frequency); output k sits in x[brev<R>(k)].
+template <int R, int DIR>
+FDAS_DEV void dft2_brev(c2 (&x)[R]) {
+#pragma unroll
+  for (int half = R / 2; half >= 1; half >>= 1) {
+#pragma unroll
+    for (int blk = 0; blk < R; blk += 2 * half) {
+#pragma unroll
+      for (int j = 0; j < half; ++j) {
+        const c2 a = x[blk + j];
+        const c2 b = x[blk + j + half];
+        x[blk + j] = c2_add(a, b);
+        x[blk + j + half] = c2_rot<DIR>(c2_sub(a, b), j, j, 2 * half);
+      }
+    }
+  }
+}
+
+// Radix-32 DFT over index e = 2 p + lane held as 16 pairs (p = 0..15,
+// lane 0 = even e, lane 1 = odd e). The first four radix-2 stages pair an
+// element with another of equal parity, so they run packed; the last stage
+// combines the two lanes of a pair and runs on scalars. On return out[e] is
+// DFT output number brev<32>(e).
+template <int DIR>
+FDAS_DEV void dft32_pairs(c2 (&x)[16], float2 (&out)[32]) {
+#pragma unroll
+  for (int half = 16; half >= 2; half >>= 1) {
+    const int hp = half / 2;  // distance in pairs
+#pragma unroll
+    for (int blk = 0; blk < 16; blk += 2 * hp) {
+#pragma unroll
+      for (int jp = 0; jp < hp; ++jp) {
+        const c2 a = x[blk + jp];
+        const c2 b = x[blk + jp + hp];
+        x[blk + jp] = c2_add(a, b);
+        x[blk + jp + hp] = c2_rot<DIR>(c2_sub(a, b), 2 * jp, 2 * jp + 1, 2 * half);
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 16; ++p) {
+    const c2 v = x[p];
+    out[2 * p] = make_float2(v.re.x + v.re.y, v.im.x + v.im.y);
+    out[2 * p + 1] = make_float2(v.re.x - v.re.y, v.im.x - v.im.y);
+  }
 }
 
 }  // namespace fdas

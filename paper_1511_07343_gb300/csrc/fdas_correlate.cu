@@ -32,54 +32,80 @@ __global__ void __launch_bounds__(kNT) k_segments(const float2* __restrict__ Xw,
   }
   __syncthreads();
   block_fft<L, kFwd, kNT, 1>(sbuf, tw, tid);
-  float2* out = seg + (size_t)s * L;
-  for (int i = tid; i < L; i += kNT) out[i] = sbuf[i];
+  // packed layout (see the correlation kernel)
+  constexpr int RA2 = L / 512;
+  float4* out = reinterpret_cast<float4*>(seg) + (size_t)s * (L / 2);
+  for (int sl = tid; sl < L / 2; sl += kNT) {
+    const int u = sl & 15, ab = sl >> 4;
+    const int a = ab % RA2, b = ab / RA2;
+    const int k0 = 2 * u + 32 * (a + RA2 * b);
+    const float2 x0 = sbuf[k0], x1 = sbuf[k0 + 1];
+    out[sl] = make_float4(x0.x, x1.x, x0.y, x1.y);
+  }
 }
+
+// Packed layout of a length-L spectrum (segments and templates alike): with
+// k = k1 + 32 k2, k1 = 2u + e (u < 16, e in {0, 1}), k2 = a + RA2 b
+// (a < RA2 = L/512, b < 16), slot (b RA2 + a) 16 + u holds the float4
+// (re[k1=2u], re[2u+1], im[2u], im[2u+1]): one 16-byte load gives a thread
+// the packed pair it transforms.
+template <int L>
+__host__ __device__ constexpr int pk_ra2() { return L / 512; }
 
 // Steps 5-7, fused: one pass per (segment, template) pair through
 //   Y = F_s * T_z  ->  inverse FFT  ->  |.|^2  ->  keep the V valid outputs,
-// with the complex plane never leaving the SM. Layout of the length-L inverse
-// FFT (L = 32 NA, NA = 16 RA2 threads):
-//   k = k1 + 32 k2, k2 = a + RA2 b;   n = n2 + NA n1, n2 = c + 16 d
-//   A1 (per thread, 2 x radix-16 over b): u = sum_b Y[k1 + 32 a + 32 RA2 b] w16^{bc},
-//      times w_NA^{ac}                                   (k1 = lane, a = warp + NW h)
-//   A2 (32/RA2 x radix-RA2 over a): Z[k1][c + 16 d], times w_L^{k1 (c + 16 d)}
-//   B  (radix-32 over k1): c[n2 + NA n1]                 (n2 = thread index)
-// Two shared-memory exchanges per pair (A1->A2, A2->B). The segment spectrum
-// F_s is held in tensor memory for the whole sweep over templates; the
-// template spectra stream from L2. Besides the plane row the kernel writes
-// the 4-bin maximum Q4[z][r/4] (used to screen the harmonic sums) and emits
-// the h = 1 candidates. Work is a static, evenly split range of pairs per
-// CTA (one wave of resident CTAs).
+// with the complex plane never leaving the SM. Length-L inverse FFT,
+// L = 32 NA, NA = 16 RA2 (= threads), n = n2 + NA n1, n2 = c + 16 d:
+//   A1 radix-16 over b of Y[k1 + 32 (a + RA2 b)], times w_NA^{a c}
+//        thread (u, a): the pair k1 = 2u, 2u+1, packed
+//   A2 radix-RA2 over a -> Z[k1][c + 16 d], times w_L^{k1 (c + 16 d)}
+//        16/RA2 packed butterflies (u, c) per thread
+//   B  radix-32 over k1 -> c[n2 + NA n1]     thread n2
+// All butterflies work on packed f32x2 pairs (two transforms per FP32
+// instruction). Two shared-memory exchanges per pair; the segment spectrum
+// and the thread's B-stage twiddles live in tensor memory for the whole
+// sweep over templates; template spectra stream from L2. Besides the plane
+// row the kernel writes the 4-bin maxima Q4[z][r/4] (used to screen the
+// harmonic sums) and emits the h = 1 candidates. Each CTA takes an evenly
+// split, contiguous range of (segment, template) pairs (one wave).
 template <int L>
 struct Corr {
   static constexpr int T = L / 32;
   static constexpr int NA = L / 32;
   static constexpr int RA2 = NA / 16;
+  static constexpr int NB2 = 16 / RA2;
   static constexpr int NW = T / 32;
-  static constexpr int XP = NA + 1;
-  static constexpr int XF = (L > 32 * XP) ? L : 32 * XP;
-  static constexpr int NCOLS = NW > 4 ? 128 : 64;
+  static constexpr int X2P = 17;  // float4 pitch of an n2 row in the A2 -> B exchange
+  static constexpr int XF4 = (L / 2 > NA * X2P) ? L / 2 : NA * X2P;
+  static constexpr int NGROUPS = (NW + 3) / 4;  // warps w and w + 4 share TMEM lanes
+  static constexpr int NCOLS = 128 * NGROUPS;   // per thread: 64 (F) + 64 (B twiddles)
   static constexpr int MAXCTA = 512 / NCOLS;
-  static constexpr int MINB = L == 8192 ? 2 : (L == 4096 ? 4 : 8);
-  static constexpr size_t SMEM = sizeof(float2) * (XF + NA) + sizeof(float) * L;
+  static constexpr int MINB = L == 8192 ? 2 : 4;
+  static constexpr size_t SMEM = 16 * (size_t)(XF4 + RA2 * 16) + 4 * (size_t)L;
 };
+
+FDAS_DEV c2 c2_of(float4 v) { return c2{make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
+FDAS_DEV float4 f4_of(c2 v) { return make_float4(v.re.x, v.re.y, v.im.x, v.im.y); }
 
 template <int L>
 __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
-    k_correlate_fused(const float2* __restrict__ seg, const float2* __restrict__ bank,
+    k_correlate_fused(const float4* __restrict__ seg4, const float4* __restrict__ bank4,
                       float* __restrict__ plane, float* __restrict__ q4, int64_t nb, int Z, int V,
                       int m, int64_t n_pairs, const float2* __restrict__ twL, float thr1,
                       fdas_cand* __restrict__ cands, unsigned long long* count, int64_t maxc) {
   using C = Corr<L>;
-  constexpr int T = C::T, NA = C::NA, RA2 = C::RA2, NW = C::NW, XP = C::XP;
-  extern __shared__ float2 smem[];
-  float2* X = smem;
-  float2* twA = smem + C::XF;  // exp(+2 pi i e / NA)
-  float* Ps = reinterpret_cast<float*>(smem + C::XF + NA);  // powers of the kept outputs
+  constexpr int T = C::T, NA = C::NA, RA2 = C::RA2, NB2 = C::NB2, X2P = C::X2P;
+  constexpr int L2 = L / 2;
+  extern __shared__ float4 smem4[];
+  float4* X = smem4;
+  float4* twA = smem4 + C::XF4;  // (c, c, s, s) of exp(+2 pi i a c / NA), a < RA2, c < 16
+  float* Ps = reinterpret_cast<float*>(twA + RA2 * 16);
   __shared__ uint32_t s_tmem;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int e = tid; e < NA; e += T) twA[e] = cconj(__ldg(twL + e * 32));
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int e = tid; e < RA2 * 16; e += T) {
+    const float2 w = cconj(__ldg(twL + (((e >> 4) * (e & 15) * 32) & (L - 1))));
+    twA[e] = make_float4(w.x, w.x, w.y, w.y);
+  }
   if (warp == 0) {
     tmem_alloc(&s_tmem, C::NCOLS);
     tmem_relinquish();
@@ -88,33 +114,51 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
   __syncthreads();
   tmem_fence_after_sync();
   const uint32_t tbase =
-      s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 64u * (uint32_t)(warp >> 2);
+      s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 128u * (uint32_t)(warp >> 2);
+  // B-stage twiddles exp(+2 pi i k1 n2 / L), k1 = 2u, 2u+1, n2 = c + 16 d, for
+  // this thread's A2 butterflies -> tensor-memory columns 64..127
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float f[16];
+#pragma unroll
+    for (int w4 = 0; w4 < 4; ++w4) {
+      const int idx = q * 4 + w4;  // = i * RA2 + d
+      const int i = idx / RA2, d = idx % RA2;
+      const int g = tid + T * i;
+      const int u = g & 15, c = g >> 4;
+      const int n2 = c + 16 * d;
+      const float2 w0 = cconj(__ldg(twL + ((2 * u * n2) & (L - 1))));
+      const float2 w1 = cconj(__ldg(twL + (((2 * u + 1) * n2) & (L - 1))));
+      f[4 * w4] = w0.x;
+      f[4 * w4 + 1] = w1.x;
+      f[4 * w4 + 2] = w0.y;
+      f[4 * w4 + 3] = w1.y;
+    }
+    tmem_st16(tbase + 64 + 16 * q, f);
+  }
+  tmem_wait_st();
 
-  // exp(+2 pi i 16 e lane / L) for e = 1, 2, 4, 8 (B-stage twiddle steps)
-  const float2 st1 = cconj(__ldg(twL + ((16 * lane) & (L - 1))));
-  const float2 st2 = cconj(__ldg(twL + ((32 * lane) & (L - 1))));
-  const float2 st4 = cconj(__ldg(twL + ((64 * lane) & (L - 1))));
-  const float2 st8 = cconj(__ldg(twL + ((128 * lane) & (L - 1))));
+  const int u1 = tid & 15, a1 = tid >> 4;  // A1 role
   const int half_m = m / 2;
   const int64_t nq = nb >> 2;
-
   const int64_t p0 = (int64_t)blockIdx.x * n_pairs / gridDim.x;
   const int64_t p1 = (int64_t)(blockIdx.x + 1) * n_pairs / gridDim.x;
   int s_cur = -1;
   for (int64_t p = p0; p < p1; ++p) {
     const int s = (int)(p / Z);
     const int z = (int)(p - (int64_t)s * Z);
-    if (s != s_cur) {  // segment spectrum -> tensor memory
-      const float2* fs = seg + (size_t)s * L;
+    if (s != s_cur) {  // segment spectrum -> tensor memory columns 0..63
+      const float4* fs = seg4 + (size_t)s * L2 + a1 * 16 + u1;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         float f[16];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int idx = q * 8 + i;
-          const float2 v = __ldg(fs + tid + T * (idx >> 4) + 2 * T * (idx & 15));
-          f[2 * i] = v.x;
-          f[2 * i + 1] = v.y;
+        for (int i = 0; i < 4; ++i) {
+          const float4 v = __ldg(fs + (q * 4 + i) * RA2 * 16);
+          f[4 * i] = v.x;
+          f[4 * i + 1] = v.y;
+          f[4 * i + 2] = v.z;
+          f[4 * i + 3] = v.w;
         }
         tmem_st16(tbase + 16 * q, f);
       }
@@ -122,78 +166,67 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
       s_cur = s;
     }
     // ---- A1
-    float2 v[2][16];
-    const float2* tz = bank + (size_t)z * L;
+    c2 v[16];
+    const float4* tz = bank4 + (size_t)z * L2 + a1 * 16 + u1;
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int b = 0; b < 16; ++b) v[h][b] = __ldg(tz + tid + T * h + 2 * T * b);
+    for (int b = 0; b < 16; ++b) v[b] = c2_of(__ldg(tz + b * RA2 * 16));
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       float f[16];
       tmem_ld16(tbase + 16 * q, f);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int idx = q * 8 + i;
-        v[idx >> 4][idx & 15] = cmul(v[idx >> 4][idx & 15], make_float2(f[2 * i], f[2 * i + 1]));
-      }
+      for (int i = 0; i < 4; ++i)
+        v[q * 4 + i] = c2_mul(v[q * 4 + i], c2{make_float2(f[4 * i], f[4 * i + 1]),
+                                              make_float2(f[4 * i + 2], f[4 * i + 3])});
+    }
+    dft2_brev<16, kInv>(v);
+#pragma unroll
+    for (int c = 1; c < 16; ++c) {
+      const float4 tw = twA[a1 * 16 + c];
+      v[brev<16>(c)] = c2_mul_cs(v[brev<16>(c)], make_float2(tw.x, tw.y), make_float2(tw.z, tw.w));
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      dft_brev<16, kInv>(v[h]);
-      const int a = warp + NW * h;
-#pragma unroll
-      for (int c = 1; c < 16; ++c)
-        v[h][brev<16>(c)] = cmul(v[h][brev<16>(c)], twA[(a * c) & (NA - 1)]);
-#pragma unroll
-      for (int c = 0; c < 16; ++c) X[(a * 16 + c) * 32 + lane] = v[h][brev<16>(c)];
-    }
+    for (int c = 0; c < 16; ++c) X[(a1 * 16 + c) * 16 + u1] = f4_of(v[brev<16>(c)]);
     __syncthreads();
     // ---- A2
-    constexpr int NB2 = 32 / RA2;
-    float2 w[NB2][RA2];
+    c2 w[NB2][RA2];
 #pragma unroll
     for (int i = 0; i < NB2; ++i) {
-      const int c = warp + NW * i;
+      const int g = tid + T * i;
+      const int u = g & 15, c = g >> 4;
 #pragma unroll
-      for (int a = 0; a < RA2; ++a) w[i][a] = X[(a * 16 + c) * 32 + lane];
+      for (int a = 0; a < RA2; ++a) w[i][a] = c2_of(X[(a * 16 + c) * 16 + u]);
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < NB2; ++i) {
-      dft_brev<RA2, kInv>(w[i]);
-      const int c = warp + NW * i;
-      float2 W[RA2];
-      W[0] = cconj(__ldg(twL + lane * c));
-      if constexpr (RA2 > 1) W[1] = cmul(W[0], st1);
-      if constexpr (RA2 > 2) {
-        W[2] = cmul(W[0], st2);
-        W[3] = cmul(W[2], st1);
-      }
-      if constexpr (RA2 > 4) {
-        W[4] = cmul(W[0], st4);
-        W[5] = cmul(W[4], st1);
-        W[6] = cmul(W[4], st2);
-        W[7] = cmul(W[6], st1);
-      }
-      if constexpr (RA2 > 8) {
+      dft2_brev<RA2, kInv>(w[i]);
+      const int g = tid + T * i;
+      const int u = g & 15, c = g >> 4;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) W[8 + k] = cmul(W[k], st8);
-      }
+      for (int d0 = 0; d0 < RA2; d0 += 4) {
+        float f[16];
+        tmem_ld16(tbase + 64 + 4 * (i * RA2 + d0), f);
 #pragma unroll
-      for (int d = 0; d < RA2; ++d) X[lane * XP + c + 16 * d] = cmul(w[i][brev<RA2>(d)], W[d]);
+        for (int dd = 0; dd < 4; ++dd) {
+          const int d = d0 + dd;
+          const c2 t = c2_mul_cs(w[i][brev<RA2>(d)], make_float2(f[4 * dd], f[4 * dd + 1]),
+                                 make_float2(f[4 * dd + 2], f[4 * dd + 3]));
+          X[(c + 16 * d) * X2P + u] = f4_of(t);
+        }
+      }
     }
     __syncthreads();
     // ---- B
-    float2 y[32];
+    c2 y[16];
 #pragma unroll
-    for (int k1 = 0; k1 < 32; ++k1) y[k1] = X[k1 * XP + tid];
-    dft_brev<32, kInv>(y);
-    // powers of the kept outputs n in [m/2, L - m/2) -> Ps[n - m/2]
+    for (int u = 0; u < 16; ++u) y[u] = c2_of(X[tid * X2P + u]);
+    float2 out[32];
+    dft32_pairs<kInv>(y, out);
 #pragma unroll
-    for (int n1 = 0; n1 < 32; ++n1) {
-      const int n = tid + NA * n1;
-      if (n >= half_m && n < L - half_m) Ps[n - half_m] = cnorm(y[brev<32>(n1)]);
+    for (int e = 0; e < 32; ++e) {
+      const int n = tid + NA * brev<32>(e);
+      if (n >= half_m && n < L - half_m) Ps[n - half_m] = cnorm(out[e]);
     }
     __syncthreads();
     // coalesced float4 stores of the plane row slice, its 4-bin maxima and
@@ -207,31 +240,44 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
     const float4* P4 = reinterpret_cast<const float4*>(Ps);
     bool hit = false;
     for (int k = tid; k < n4; k += T) {
-      const float4 v4 = P4[k];
-      if (prow) reinterpret_cast<float4*>(prow)[k] = v4;
-      if (qrow) qrow[k] = fmaxf(fmaxf(v4.x, v4.y), fmaxf(v4.z, v4.w));
-      hit |= fmaxf(fmaxf(v4.x, v4.y), fmaxf(v4.z, v4.w)) >= thr1;
+      const float4 p4 = P4[k];
+      const float mx = fmaxf(fmaxf(p4.x, p4.y), fmaxf(p4.z, p4.w));
+      if (prow) reinterpret_cast<float4*>(prow)[k] = p4;
+      if (qrow) qrow[k] = mx;
+      hit |= mx >= thr1;
     }
     if (cands && __syncthreads_or(hit)) {
       // rare: some power reached T_1; scan the slice again and append
       for (int k0 = 0; k0 < n4; k0 += T) {
         const int k = k0 + tid;
         const bool in = k < n4;
-        const float4 v4 = in ? P4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 p4 = in ? P4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
         const int rk = (int)(r0 + 4 * k);
-        emit(in && rk >= 1 && v4.x >= thr1, rk, z, 1, v4.x, cands, count, maxc);
-        emit(in && v4.y >= thr1, rk + 1, z, 1, v4.y, cands, count, maxc);
-        emit(in && v4.z >= thr1, rk + 2, z, 1, v4.z, cands, count, maxc);
-        emit(in && v4.w >= thr1, rk + 3, z, 1, v4.w, cands, count, maxc);
+        emit(in && rk >= 1 && p4.x >= thr1, rk, z, 1, p4.x, cands, count, maxc);
+        emit(in && p4.y >= thr1, rk + 1, z, 1, p4.y, cands, count, maxc);
+        emit(in && p4.z >= thr1, rk + 2, z, 1, p4.z, cands, count, maxc);
+        emit(in && p4.w >= thr1, rk + 3, z, 1, p4.w, cands, count, maxc);
       }
     }
-    // no barrier needed here: the next pair's first writes to X come after
-    // its own A1 work, and its Ps writes after three more barriers
+    // the next pair's first shared-memory writes follow three more barriers
   }
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
   if (warp == 0) tmem_dealloc(s_tmem, C::NCOLS);
+}
+
+// Natural-order copy of the packed template bank (for export).
+template <int L>
+__global__ void k_bank_natural(const float* __restrict__ bankf, float2* __restrict__ out, int Z) {
+  constexpr int RA2 = pk_ra2<L>();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)Z * L) return;
+  const int j = (int)(i / L), k = (int)(i % L);
+  const int e = k & 1, u = (k & 31) >> 1, k2 = k >> 5;
+  const int slot = ((k2 / RA2) * RA2 + (k2 % RA2)) * 16 + u;
+  const float* f = bankf + ((size_t)j * (L / 2) + slot) * 4;
+  out[i] = make_float2(f[e], f[2 + e]);
 }
 
 template <int L>
@@ -285,12 +331,29 @@ int corr_launch(fdas_plan* p, float* plane, float* q4, fdas_cand* cands,
   if (grid > n_pairs) grid = n_pairs;
   p->corr_grid = (int)grid;
   k_correlate_fused<L><<<(unsigned)grid, C::T, smem, p->stream>>>(
-      p->seg, p->bank, plane, q4, p->nb, p->Z, p->V, p->m, n_pairs, p->tw_L, p->thr[0], cands,
-      count, p->max_cands);
+      reinterpret_cast<const float4*>(p->seg), reinterpret_cast<const float4*>(p->bank), plane,
+      q4, p->nb, p->Z, p->V, p->m, n_pairs, p->tw_L, p->thr[0], cands, count, p->max_cands);
   return cuda_check(cudaGetLastError(), "k_correlate_fused");
 }
 
+template <int L>
+int bank_natural_launch(fdas_plan* p, float2* out) {
+  const int64_t n = (int64_t)p->Z * L;
+  k_bank_natural<L><<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(
+      reinterpret_cast<const float*>(p->bank), out, p->Z);
+  return cuda_check(cudaGetLastError(), "k_bank_natural");
+}
+
 }  // namespace
+
+int launch_bank_natural(fdas_plan* p, float2* d_out) {
+  switch (p->L) {
+    case 2048: return bank_natural_launch<2048>(p, d_out);
+    case 4096: return bank_natural_launch<4096>(p, d_out);
+    case 8192: return bank_natural_launch<8192>(p, d_out);
+  }
+  return set_error(FDAS_ERR_INVALID, "unsupported segment length");
+}
 
 int launch_segments(fdas_plan* p, const float2* d_white) {
   switch (p->L) {

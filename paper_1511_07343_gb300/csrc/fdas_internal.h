@@ -32,7 +32,7 @@ struct fdas_plan {
 
   // templates
   double2* taps = nullptr;     // Z x m float64 taps
-  float2* bank = nullptr;      // Z x L spectra, 1/L folded in
+  float2* bank = nullptr;      // Z x L spectra, 1/L folded in, packed layout (correlate)
 
   // per-trial workspaces
   float* series = nullptr;     // N floats (host-input staging)
@@ -40,7 +40,7 @@ struct fdas_plan {
   float2* spec = nullptr;      // nb complex spectrum
   float2* spec2 = nullptr;     // M complex packed FFT (before the real-FFT unpack)
   float2* white = nullptr;     // nb complex whitened spectrum
-  float2* seg = nullptr;       // S x L segment spectra
+  float2* seg = nullptr;       // S x L segment spectra, packed layout (correlate)
   float* plane = nullptr;      // Z x nb power plane
   float* q4 = nullptr;         // Z x nb/4 maxima of 4 consecutive plane bins
   fdas_cand* cands = nullptr;  // max_cands
@@ -69,6 +69,7 @@ int launch_whiten(fdas_plan* p, const float2* d_spec, float2* d_white);
 
 // fdas_correlate.cu
 int launch_segments(fdas_plan* p, const float2* d_white);
+int launch_bank_natural(fdas_plan* p, float2* d_out);
 int launch_correlate(fdas_plan* p, float* d_plane, float* d_q4, fdas_cand* d_cands,
                      unsigned long long* d_count);
 

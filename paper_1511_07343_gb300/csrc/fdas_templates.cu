@@ -189,7 +189,14 @@ __global__ void k_template_bank(const double2* __restrict__ taps, float2* __rest
     w = w * step;
   }
   const double inv = 1.0 / (double)L;
-  bank[(size_t)j * L + k] = make_float2((float)(acc.re * inv), (float)(acc.im * inv));
+  // packed layout: slot ((k2 / RA2) RA2 + k2 % RA2) 16 + u holds
+  // (re[2u], re[2u+1], im[2u], im[2u+1]) with k = (2u + e) + 32 k2
+  const int RA2 = L / 512;
+  const int e = k & 1, u = (k & 31) >> 1, k2 = k >> 5;
+  const int slot = ((k2 / RA2) * RA2 + (k2 % RA2)) * 16 + u;
+  float* f = reinterpret_cast<float*>(bank) + ((size_t)j * (L / 2) + slot) * 4;
+  f[e] = (float)(acc.re * inv);
+  f[2 + e] = (float)(acc.im * inv);
 }
 
 // out[i] = exp(-2 pi i ((i * mult) mod period) / period), float64 -> float32.
