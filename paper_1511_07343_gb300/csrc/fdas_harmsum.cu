@@ -51,11 +51,14 @@ __global__ void __launch_bounds__(256) k_pool4(const float* __restrict__ P, floa
 // R0 .. R0 + 16383 (R0 a multiple of 16384); thread t owns the 64 bins
 // R0 + 64 t + i. For fraction q the sub-harmonic bin is
 //     rr = round(q r / 16) = q R0/16 + 4 q t + K(q, i),  K(q, i) = (2 q i + 16) >> 5,
-// so its 4-bin group is q R0/64 + q t + (K(q, i) >> 2): a compile-time offset
-// from q t once the block's slice of row jz(q) of Q4 is staged in shared
-// memory (coalesced loads, one entry per word, padded against bank
-// conflicts). Every term is bounded by its group maximum and each pair of
-// adjacent bins shares one bound (the larger of its two groups); float
+// so its 4-bin group, relative to the block's first, is q t + (K(q, i) >> 2):
+// a compile-time offset from q t. The block's slice of row jz(q) of Q4
+// (256 q + 1 groups) is staged in shared memory split into 2^a classes by
+// index mod 2^a (q = 2^a b, b odd): lanes then read at stride b, which is
+// odd, so the reads are free of bank conflicts, and both the coalesced copy
+// (cp.async, two buffers ahead) and the reads use per-thread bases plus
+// compile-time offsets. Each term is bounded by its group maximum, each pair
+// of adjacent bins shares one bound (the larger of its groups); float
 // addition is monotone, so a pair whose running bound stays below T_h cannot
 // hold a candidate at level h. The rare flagged pairs are summed exactly from
 // P in the same order and compared with T_h.
@@ -64,13 +67,19 @@ __host__ __device__ constexpr int frac_order(int i) {
                                                                      : 1 + 2 * (i - 8);
 }
 __host__ __device__ constexpr int kq(int q, int i) { return (2 * q * i + 16) >> 5; }
-__device__ __forceinline__ int spad(int e) { return e + (e >> 5); }
+__host__ __device__ constexpr int ctz5(int q) {
+  return (q & 1) ? 0 : (q & 2) ? 1 : (q & 4) ? 2 : (q & 8) ? 3 : 4;
+}
+// words between classes for fraction q (a >= 1): room for 256 b + 1 entries,
+// rounded to 32, then skewed so that the 2^a classes start on distinct banks
+__host__ __device__ constexpr int class_stride(int q) {
+  return 256 * (q >> ctz5(q)) + 32 + (32 >> ctz5(q));
+}
 
 constexpr int kHsThreads = 256;
 constexpr int kHsCells = 64;
 constexpr int kHsSpan = kHsThreads * kHsCells;
-constexpr int kStageN = 16 * kHsThreads + 1;            // entries staged for q = 16
-constexpr int kStageW = kStageN + (kStageN >> 5) + 1;   // padded words
+constexpr int kStageW = 16 * (256 + 32 + 2);  // largest staged slice (q = 16)
 constexpr size_t kHsSmem = 3 * kStageW * sizeof(float);
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
@@ -86,59 +95,54 @@ __device__ __forceinline__ void cp_async_wait1() {
   asm volatile("cp.async.wait_group 1;" ::: "memory");
 }
 
-template <int NLEV>
-__global__ void __launch_bounds__(kHsThreads) k_harmsum_staged(
-    const float* __restrict__ P, const float* __restrict__ Q4, int64_t nb, int Z, Thr thr,
-    fdas_cand* __restrict__ out, unsigned long long* count, int64_t maxc) {
-  constexpr int NQ = 1 << (NLEV - 1);
-  extern __shared__ float stage[];  // 3 x kStageW, rotating
-  const int j = blockIdx.y;
-  const int64_t R0 = (int64_t)blockIdx.x * kHsSpan;
-  const int tid = threadIdx.x;
-  const int64_t nq = nb >> 2;
-  const int zc = (Z - 1) / 2;
-  const int jc = j - zc;
-  const int ajc = jc < 0 ? -jc : jc;
-  const int sg = jc < 0 ? -1 : 1;
-  // asynchronous copy of the block's slice of row jz(q) of Q4 (fraction
-  // number oi in summation order) into rotating buffer oi % 3
-  auto issue = [&](int oi) {
-    if (oi < NQ) {
-      const int q = frac_order(oi);
-      float* sb = stage + (oi % 3) * kStageW;
-      const int row = zc + sg * ((2 * q * ajc + 16) >> 5);
-      const int64_t e_lo = (int64_t)q * (R0 >> 6);
-      const int cnt = kHsThreads * q + 1;
-      const float* src = Q4 + (size_t)row * nq + e_lo;
-      for (int e = tid; e < cnt; e += kHsThreads) {
-        const bool ok = e_lo + e < nq;
-        cp_async4(sb + spad(e), ok ? src + e : Q4, ok);
-      }
-    }
-    cp_async_commit();
-  };
-  float acc[kHsCells / 2];
-  unsigned pmask = 0;
-  issue(0);
-  issue(1);
+struct HsCtx {
+  float* stage;
+  const float* Q4;
+  int64_t nq, R0;
+  int tid, zc, sg, ajc;
+};
+
+// copy of the block's slice of row jz(q) of Q4 (fraction number OI in
+// summation order) into rotating buffer OI % 3, class-split
+template <int OI, int NQ>
+FDAS_DEV void hs_issue(const HsCtx& x) {
+  if constexpr (OI < NQ) {
+    constexpr int q = frac_order(OI);
+    constexpr int a = ctz5(q), m = (1 << a) - 1;
+    constexpr int CS = class_stride(q);
+    float* sb = x.stage + (OI % 3) * kStageW + (x.tid & m) * CS + (x.tid >> a);
+    const int row = x.zc + x.sg * ((2 * q * x.ajc + 16) >> 5);
+    const int64_t e_lo = (int64_t)q * (x.R0 >> 6);
+    const float* src = x.Q4 + (size_t)row * x.nq + e_lo + x.tid;
+    const int64_t lim = x.nq - e_lo - x.tid;  // element k is in bounds while 256 k < lim
 #pragma unroll
-  for (int oi = 0; oi < NQ; ++oi) {
-    const int q = frac_order(oi);
+    for (int k = 0; k < q; ++k) cp_async4(sb + k * (256 >> a), src + 256 * k, 256 * k < lim);
+    if (x.tid == 0) cp_async4(sb + q * (256 >> a), src + 256 * q, 256 * q < lim);
+  }
+  cp_async_commit();
+}
+
+template <int OI, int NQ>
+FDAS_DEV void hs_steps(const HsCtx& x, float (&acc)[kHsCells / 2], unsigned& pmask,
+                       const Thr& thr) {
+  if constexpr (OI < NQ) {
+    constexpr int q = frac_order(OI);
+    constexpr int a = ctz5(q), m = (1 << a) - 1, b = q >> a;
+    constexpr int CS = class_stride(q);
     cp_async_wait1();
     __syncthreads();
-    issue(oi + 2);
-    const float* sb = stage + (oi % 3) * kStageW;
-    const int base = q * tid;
+    hs_issue<OI + 2, NQ>(x);
+    const float* sb = x.stage + (OI % 3) * kStageW + b * x.tid;
 #pragma unroll
     for (int pr = 0; pr < kHsCells / 2; ++pr) {
       const int o1 = kq(q, 2 * pr) >> 2;
       const int o2 = kq(q, 2 * pr + 1) >> 2;
-      float v = sb[spad(base + o1)];
-      if (o2 != o1) v = fmaxf(v, sb[spad(base + o2)]);
-      acc[pr] = (oi == 0) ? v : acc[pr] + v;
+      float v = sb[(o1 & m) * CS + (o1 >> a)];
+      if (o2 != o1) v = fmaxf(v, sb[(o2 & m) * CS + (o2 >> a)]);
+      acc[pr] = (OI == 0) ? v : acc[pr] + v;
     }
-    if (oi == 1 || oi == 3 || oi == 7 || oi == 15) {
-      const int lvl = oi == 1 ? 1 : (oi == 3 ? 2 : (oi == 7 ? 3 : 4));
+    if constexpr (OI == 1 || OI == 3 || OI == 7 || OI == 15) {
+      constexpr int lvl = OI == 1 ? 1 : (OI == 3 ? 2 : (OI == 7 ? 3 : 4));
       const float t = thr.t[lvl];
       float mx = acc[0];
 #pragma unroll
@@ -149,7 +153,34 @@ __global__ void __launch_bounds__(kHsThreads) k_harmsum_staged(
           if (acc[pr] >= t) pmask |= 1u << pr;
       }
     }
+    hs_steps<OI + 1, NQ>(x, acc, pmask, thr);
   }
+}
+
+template <int NLEV>
+__global__ void __launch_bounds__(kHsThreads) k_harmsum_staged(
+    const float* __restrict__ P, const float* __restrict__ Q4, int64_t nb, int Z, Thr thr,
+    fdas_cand* __restrict__ out, unsigned long long* count, int64_t maxc) {
+  constexpr int NQ = 1 << (NLEV - 1);
+  extern __shared__ float stage[];  // 3 x kStageW, rotating
+  const int j = blockIdx.y;
+  HsCtx x;
+  x.stage = stage;
+  x.Q4 = Q4;
+  x.nq = nb >> 2;
+  x.R0 = (int64_t)blockIdx.x * kHsSpan;
+  x.tid = threadIdx.x;
+  x.zc = (Z - 1) / 2;
+  const int jc = j - x.zc;
+  x.ajc = jc < 0 ? -jc : jc;
+  x.sg = jc < 0 ? -1 : 1;
+  const int zc = x.zc, sg = x.sg, ajc = x.ajc, tid = x.tid;
+  const int64_t R0 = x.R0;
+  float acc[kHsCells / 2];
+  unsigned pmask = 0;
+  hs_issue<0, NQ>(x);
+  hs_issue<1, NQ>(x);
+  hs_steps<0, NQ>(x, acc, pmask, thr);
   // pairs past the end of the spectrum
   const int64_t first = R0 + (int64_t)kHsCells * tid;
   if (first >= nb) pmask = 0;

@@ -129,14 +129,15 @@ int dispatch_rows(fdas_plan* p, const float2* T, float2* Zo) {
 // ----------------------------------------------------------------------------
 // Whitening: mu_k = even-count median of |X|^2 over the 64-bin window of bin
 // k ([k-32, k+31] shifted into [1, nb-1]); Xw_k = X_k sqrt(ln2 / mu_k).
-// A CTA takes 256 consecutive bins: the union of their windows (<= 319
-// powers) is sorted once in shared memory (bitonic, 512 slots), and each
-// thread walks the sorted list picking the 32nd and 33rd entries that fall in
-// its own window.
+// A CTA takes 128 consecutive bins: the union of their windows (<= 191
+// powers) is sorted once in shared memory as 64-bit keys (power bits, then
+// index; powers are >= 0 so their bit patterns order like the values), and
+// each thread walks the sorted list picking the 32nd and 33rd entries that
+// fall in its own window.
 // ----------------------------------------------------------------------------
 constexpr int kWin = 64;
-constexpr int kWTile = 256;
-constexpr int kSortN = 512;
+constexpr int kWTile = 128;
+constexpr int kSortN = 256;
 
 __device__ __forceinline__ int64_t wstart(int64_t k, int64_t nb) {
   int64_t s = k - kWin / 2;
@@ -146,8 +147,7 @@ __device__ __forceinline__ int64_t wstart(int64_t k, int64_t nb) {
 
 __global__ void __launch_bounds__(kWTile) k_whiten(const float2* __restrict__ X,
                                                    float2* __restrict__ Xw, int64_t nb) {
-  __shared__ float skey[kSortN];
-  __shared__ int sidx[kSortN];
+  __shared__ unsigned long long skey[kSortN];
   const int tid = threadIdx.x;
   const int64_t k0 = (int64_t)blockIdx.x * kWTile;
   const int64_t klast = (k0 + kWTile - 1 < nb - 1) ? k0 + kWTile - 1 : nb - 1;
@@ -155,28 +155,22 @@ __global__ void __launch_bounds__(kWTile) k_whiten(const float2* __restrict__ X,
   const int64_t hi = wstart(klast, nb) + kWin - 1;
   const int cnt = (int)(hi - lo + 1);
   for (int t = tid; t < kSortN; t += kWTile) {
-    if (t < cnt) {
-      skey[t] = cnorm(X[lo + t]);
-      sidx[t] = t;
-    } else {
-      skey[t] = FLT_MAX;
-      sidx[t] = 1 << 30;
-    }
+    unsigned long long key = ~0ull;
+    if (t < cnt)
+      key = ((unsigned long long)__float_as_uint(cnorm(X[lo + t])) << 32) | (unsigned)t;
+    skey[t] = key;
   }
   __syncthreads();
-  // bitonic sort, ascending, 256 threads x one compare-exchange each
+  // bitonic sort, ascending, one compare-exchange per thread per step
   for (int size = 2; size <= kSortN; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       const int a = 2 * stride * (tid / stride) + (tid % stride);
       const int b = a + stride;
       const bool up = (a & size) == 0;
-      const float ka = skey[a], kb = skey[b];
+      const unsigned long long ka = skey[a], kb = skey[b];
       if ((ka > kb) == up) {
         skey[a] = kb;
         skey[b] = ka;
-        const int ia = sidx[a];
-        sidx[a] = sidx[b];
-        sidx[b] = ia;
       }
       __syncthreads();
     }
@@ -187,21 +181,21 @@ __global__ void __launch_bounds__(kWTile) k_whiten(const float2* __restrict__ X,
     Xw[0] = make_float2(0.f, 0.f);
     return;
   }
-  const int s = (int)(wstart(k, nb) - lo);
-  float va = 0.f, vb = 0.f;
+  const unsigned s = (unsigned)(wstart(k, nb) - lo);
+  unsigned va = 0, vb = 0;
   int c = 0;
   for (int t = 0; t < cnt; ++t) {
-    const int id = sidx[t];
-    if (id >= s && id < s + kWin) {
-      if (c == kWin / 2 - 1) va = skey[t];
+    const unsigned long long key = skey[t];
+    if ((unsigned)key - s < (unsigned)kWin) {  // index in [s, s + 63]
+      if (c == kWin / 2 - 1) va = (unsigned)(key >> 32);
       if (c == kWin / 2) {
-        vb = skey[t];
+        vb = (unsigned)(key >> 32);
         break;
       }
       ++c;
     }
   }
-  const float mu = 0.5f * (va + vb);
+  const float mu = 0.5f * (__uint_as_float(va) + __uint_as_float(vb));
   const float2 x = X[k];
   const float g = mu > 0.f ? sqrtf(0.69314718055994531f / mu) : 0.f;
   Xw[k] = make_float2(x.x * g, x.y * g);
