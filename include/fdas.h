@@ -138,6 +138,24 @@ int fdas_template_bank(fdas_plan* plan, float* d_bank);
  * (steps 5-7), harmonic sum + threshold + compaction. */
 int fdas_profile_trial(fdas_plan* plan, const float* d_series, float* h_ms);
 
+/* Real FFT of one series without a plan and without allocating device memory.
+ * The paper has no counterpart; this exists for callers that must not
+ * allocate device memory (for example a real-time loop with a fixed device
+ * footprint, or a host framework that owns the device allocator) and so
+ * cannot create a plan. Computes the same X_k as fdas_stage_spectrum,
+ * k = 0..N/2-1, from d_series (N floats, device) into d_spectrum (N/2 float2,
+ * device), asynchronously on `stream` (a cudaStream_t, may be NULL).
+ *   N: power of two, 2^12 <= N <= 2^20; larger N returns FDAS_ERR_INVALID.
+ * Scratch: a fixed 8.5 MB array in device memory that every GPU loading this
+ * library holds until the process exits; no call allocates or frees memory.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture. All
+ * calls share the one array: calls whose work overlaps on a GPU (different
+ * streams or host threads) race and give wrong results; serialise them.
+ * Every value the kernels read from the array is written earlier in the same
+ * call, so nothing needs clearing between calls. */
+int fdas_spectrum_noalloc(const float* d_series, int64_t N, float* d_spectrum, void* stream);
+
 /* Host-side Fresnel integrals C(x), S(x) of the library's own float64
  * implementation (the one the template kernel runs), for CPU checks. */
 int fdas_host_fresnel(double x, double* C, double* S);

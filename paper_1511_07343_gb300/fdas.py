@@ -68,6 +68,7 @@ _SIGS = {
     "fdas_template_taps": [_P, _P],
     "fdas_template_bank": [_P, _P],
     "fdas_profile_trial": [_P, _P, _P],
+    "fdas_spectrum_noalloc": [_P, _I64, _P, _P],
     "fdas_host_fresnel": [ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_double)],
 }
@@ -188,6 +189,11 @@ def fdas_profile_trial(plan, d_series):
     ms = np.zeros(5, dtype=np.float32)
     _check(load().fdas_profile_trial(plan, _ptr(d_series), ms.ctypes.data), "fdas_profile_trial")
     return ms
+
+
+def fdas_spectrum_noalloc(d_series, N, d_spectrum, stream=0):
+    _check(load().fdas_spectrum_noalloc(_ptr(d_series), N, _ptr(d_spectrum), _ptr(stream) or None),
+           "fdas_spectrum_noalloc")
 
 
 def fdas_host_fresnel(x: float):
