@@ -47,21 +47,21 @@ __global__ void __launch_bounds__(256) k_pool4(const float* __restrict__ P, floa
 // Harmonic sums h >= 2, screened, in a fixed summation order: the fractions
 // q/16 are added one after the other as q = 16, 8 | 4, 12 | 2, 6, 10, 14 |
 // 1, 3, .., 15, so H_2, H_4, H_8 and H_16 are the running sums after 2, 4, 8
-// and 16 terms. A block takes top row j and 16384 consecutive top bins
-// R0 .. R0 + 16383 (R0 a multiple of 16384); thread t owns the 64 bins
-// R0 + 64 t + i. For fraction q the sub-harmonic bin is
-//     rr = round(q r / 16) = q R0/16 + 4 q t + K(q, i),  K(q, i) = (2 q i + 16) >> 5,
-// so its 4-bin group, relative to the block's first, is q t + (K(q, i) >> 2):
-// a compile-time offset from q t. The block's slice of row jz(q) of Q4
-// (256 q + 1 groups) is staged in shared memory split into 2^a classes by
+// and 16 terms. A block takes top row j and 16384 consecutive top bins;
+// warp w takes the 2048 bins from R0w = R0 + 2048 w and lane l the 64 bins
+// R0w + 64 l + i. For fraction q the sub-harmonic bin is
+//     rr = round(q r / 16) = q R0w/16 + 4 q l + K(q, i),  K(q, i) = (2 q i + 16) >> 5,
+// so its 4-bin group, relative to the warp's first, is q l + (K(q, i) >> 2):
+// a compile-time offset from q l. Each warp stages its own slice of row
+// jz(q) of Q4 (32 q + 1 groups) in shared memory, split into 2^a classes by
 // index mod 2^a (q = 2^a b, b odd): lanes then read at stride b, which is
-// odd, so the reads are free of bank conflicts, and both the coalesced copy
-// (cp.async, two buffers ahead) and the reads use per-thread bases plus
-// compile-time offsets. Each term is bounded by its group maximum, each pair
-// of adjacent bins shares one bound (the larger of its groups); float
-// addition is monotone, so a pair whose running bound stays below T_h cannot
-// hold a candidate at level h. The rare flagged pairs are summed exactly from
-// P in the same order and compared with T_h.
+// odd, so reads are free of bank conflicts; copies are coalesced cp.async
+// (16-byte for odd q, whose slice is contiguous), two fractions ahead, and
+// warps never wait for one another. Each term is bounded by its group
+// maximum, each pair of adjacent bins shares one bound (the larger of its
+// groups); float addition is monotone, so a pair whose running bound stays
+// below T_h cannot hold a candidate at level h. The rare flagged pairs are
+// summed exactly from P in the same order and compared with T_h.
 __host__ __device__ constexpr int frac_order(int i) {
   return i == 0 ? 16 : i == 1 ? 8 : i == 2 ? 4 : i == 3 ? 12 : i < 8 ? 2 + 4 * (i - 4)
                                                                      : 1 + 2 * (i - 8);
@@ -70,22 +70,30 @@ __host__ __device__ constexpr int kq(int q, int i) { return (2 * q * i + 16) >> 
 __host__ __device__ constexpr int ctz5(int q) {
   return (q & 1) ? 0 : (q & 2) ? 1 : (q & 4) ? 2 : (q & 8) ? 3 : 4;
 }
-// words between classes for fraction q (a >= 1): room for 256 b + 1 entries,
-// rounded to 32, then skewed so that the 2^a classes start on distinct banks
+// words between classes (a >= 1): >= 32 b + 1 entries and = 32 >> a mod 32,
+// so the 2^a classes of one copy round start on distinct banks
 __host__ __device__ constexpr int class_stride(int q) {
-  return 256 * (q >> ctz5(q)) + 32 + (32 >> ctz5(q));
+  return 32 * (q >> ctz5(q)) + (32 >> ctz5(q));
 }
 
 constexpr int kHsThreads = 256;
+constexpr int kHsWarps = kHsThreads / 32;
 constexpr int kHsCells = 64;
 constexpr int kHsSpan = kHsThreads * kHsCells;
-constexpr int kStageW = 16 * (256 + 32 + 2);  // largest staged slice (q = 16)
-constexpr size_t kHsSmem = 3 * kStageW * sizeof(float);
+constexpr int kWarpSpan = 32 * kHsCells;
+constexpr int kStageW = 16 * 34;  // largest staged slice per warp (q = 16), floats
+constexpr size_t kHsSmem = (size_t)3 * kStageW * kHsWarps * sizeof(float);
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src),
                "r"(ok ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool ok) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+               "r"(ok ? 16 : 0)
                : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
@@ -96,63 +104,87 @@ __device__ __forceinline__ void cp_async_wait1() {
 }
 
 struct HsCtx {
-  float* stage;
+  float* stage;  // this warp's 3 rotating buffers
   const float* Q4;
-  int64_t nq, R0;
-  int tid, zc, sg, ajc;
+  int64_t nq, R0w;
+  int lane, zc, sg, ajc;
 };
 
-// copy of the block's slice of row jz(q) of Q4 (fraction number OI in
-// summation order) into rotating buffer OI % 3, class-split
+// copy of the warp's slice of row jz(q) of Q4 (fraction number OI in
+// summation order) into rotating buffer OI % 3
 template <int OI, int NQ>
 FDAS_DEV void hs_issue(const HsCtx& x) {
   if constexpr (OI < NQ) {
     constexpr int q = frac_order(OI);
     constexpr int a = ctz5(q), m = (1 << a) - 1;
-    constexpr int CS = class_stride(q);
-    float* sb = x.stage + (OI % 3) * kStageW + (x.tid & m) * CS + (x.tid >> a);
+    float* buf = x.stage + (OI % 3) * kStageW;
     const int row = x.zc + x.sg * ((2 * q * x.ajc + 16) >> 5);
-    const int64_t e_lo = (int64_t)q * (x.R0 >> 6);
-    const float* src = x.Q4 + (size_t)row * x.nq + e_lo + x.tid;
-    const int64_t lim = x.nq - e_lo - x.tid;  // element k is in bounds while 256 k < lim
+    const int64_t e_lo = (int64_t)q * (x.R0w >> 6);
+    const float* src = x.Q4 + (size_t)row * x.nq + e_lo;
+    const int64_t lim = x.nq - e_lo;  // entries e < lim exist
+    if constexpr (a == 0) {
+      // contiguous slice of 32 q + 1 entries: 16-byte chunks (nq is a
+      // multiple of 4, so a chunk is entirely inside or outside the row)
+      constexpr int nchunk = (32 * q + 1 + 3) / 4;
 #pragma unroll
-    for (int k = 0; k < q; ++k) cp_async4(sb + k * (256 >> a), src + 256 * k, 256 * k < lim);
-    if (x.tid == 0) cp_async4(sb + q * (256 >> a), src + 256 * q, 256 * q < lim);
+      for (int c0 = 0; c0 < nchunk; c0 += 32) {
+        const int c = c0 + x.lane;
+        if (c0 + 32 <= nchunk || c < nchunk) cp_async16(buf + 4 * c, src + 4 * c, 4 * c < lim);
+      }
+    } else {
+      constexpr int CS = class_stride(q);
+      float* sb = buf + (x.lane & m) * CS + (x.lane >> a);
+      const float* sl = src + x.lane;
+      const int64_t llim = lim - x.lane;
+#pragma unroll
+      for (int k = 0; k < q; ++k) cp_async4(sb + k * (32 >> a), sl + 32 * k, 32 * k < llim);
+      if (x.lane == 0) cp_async4(sb + q * (32 >> a), sl + 32 * q, 32 * q < llim);
+    }
   }
   cp_async_commit();
 }
 
 template <int OI, int NQ>
-FDAS_DEV void hs_steps(const HsCtx& x, float (&acc)[kHsCells / 2], unsigned& pmask,
+FDAS_DEV void hs_steps(const HsCtx& x, float2 (&acc)[kHsCells / 4], unsigned& pmask,
                        const Thr& thr) {
   if constexpr (OI < NQ) {
     constexpr int q = frac_order(OI);
     constexpr int a = ctz5(q), m = (1 << a) - 1, b = q >> a;
-    constexpr int CS = class_stride(q);
+    constexpr int CS = a == 0 ? 0 : class_stride(q);
     cp_async_wait1();
-    __syncthreads();
+    __syncwarp();
     hs_issue<OI + 2, NQ>(x);
-    const float* sb = x.stage + (OI % 3) * kStageW + b * x.tid;
+    const float* sb = x.stage + (OI % 3) * kStageW + b * x.lane;
 #pragma unroll
-    for (int pr = 0; pr < kHsCells / 2; ++pr) {
-      const int o1 = kq(q, 2 * pr) >> 2;
-      const int o2 = kq(q, 2 * pr + 1) >> 2;
-      float v = sb[(o1 & m) * CS + (o1 >> a)];
-      if (o2 != o1) v = fmaxf(v, sb[(o2 & m) * CS + (o2 >> a)]);
-      acc[pr] = (OI == 0) ? v : acc[pr] + v;
+    for (int pp = 0; pp < kHsCells / 4; ++pp) {
+      float v[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int pr = 2 * pp + h;
+        const int o1 = kq(q, 2 * pr) >> 2;
+        const int o2 = kq(q, 2 * pr + 1) >> 2;
+        v[h] = sb[(o1 & m) * CS + (o1 >> a)];
+        if (o2 != o1) v[h] = fmaxf(v[h], sb[(o2 & m) * CS + (o2 >> a)]);
+      }
+      const float2 v2 = make_float2(v[0], v[1]);
+      acc[pp] = (OI == 0) ? v2 : __fadd2_rn(acc[pp], v2);
     }
     if constexpr (OI == 1 || OI == 3 || OI == 7 || OI == 15) {
       constexpr int lvl = OI == 1 ? 1 : (OI == 3 ? 2 : (OI == 7 ? 3 : 4));
       const float t = thr.t[lvl];
-      float mx = acc[0];
+      float mx = fmaxf(acc[0].x, acc[0].y);
 #pragma unroll
-      for (int pr = 1; pr < kHsCells / 2; ++pr) mx = fmaxf(mx, acc[pr]);
+      for (int pp = 1; pp < kHsCells / 4; ++pp) mx = fmaxf(mx, fmaxf(acc[pp].x, acc[pp].y));
       if (mx >= t) {
 #pragma unroll
-        for (int pr = 0; pr < kHsCells / 2; ++pr)
-          if (acc[pr] >= t) pmask |= 1u << pr;
+        for (int pp = 0; pp < kHsCells / 4; ++pp) {
+          if (acc[pp].x >= t) pmask |= 1u << (2 * pp);
+          if (acc[pp].y >= t) pmask |= 1u << (2 * pp + 1);
+        }
       }
     }
+    // the next step overwrites buffer (OI + 3) % 3 = OI % 3 only after its
+    // own wait and warp barrier, which every lane reaches after these reads
     hs_steps<OI + 1, NQ>(x, acc, pmask, thr);
   }
 }
@@ -162,27 +194,27 @@ __global__ void __launch_bounds__(kHsThreads) k_harmsum_staged(
     const float* __restrict__ P, const float* __restrict__ Q4, int64_t nb, int Z, Thr thr,
     fdas_cand* __restrict__ out, unsigned long long* count, int64_t maxc) {
   constexpr int NQ = 1 << (NLEV - 1);
-  extern __shared__ float stage[];  // 3 x kStageW, rotating
+  extern __shared__ __align__(16) float stage[];  // per warp: 3 rotating buffers
   const int j = blockIdx.y;
+  const int warp = threadIdx.x >> 5;
   HsCtx x;
-  x.stage = stage;
+  x.stage = stage + warp * 3 * kStageW;
   x.Q4 = Q4;
   x.nq = nb >> 2;
-  x.R0 = (int64_t)blockIdx.x * kHsSpan;
-  x.tid = threadIdx.x;
+  x.R0w = (int64_t)blockIdx.x * kHsSpan + (int64_t)kWarpSpan * warp;
+  x.lane = threadIdx.x & 31;
   x.zc = (Z - 1) / 2;
   const int jc = j - x.zc;
   x.ajc = jc < 0 ? -jc : jc;
   x.sg = jc < 0 ? -1 : 1;
-  const int zc = x.zc, sg = x.sg, ajc = x.ajc, tid = x.tid;
-  const int64_t R0 = x.R0;
-  float acc[kHsCells / 2];
+  const int zc = x.zc, sg = x.sg, ajc = x.ajc;
+  float2 acc[kHsCells / 4];
   unsigned pmask = 0;
   hs_issue<0, NQ>(x);
   hs_issue<1, NQ>(x);
   hs_steps<0, NQ>(x, acc, pmask, thr);
   // pairs past the end of the spectrum
-  const int64_t first = R0 + (int64_t)kHsCells * tid;
+  const int64_t first = x.R0w + (int64_t)kHsCells * x.lane;
   if (first >= nb) pmask = 0;
   else if (first + kHsCells > nb) pmask &= (1u << ((nb - first) >> 1)) - 1u;
   // exact sums of the flagged pairs, same order as the bound
