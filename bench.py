@@ -127,6 +127,64 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
+def reduce_max(value, world, device=None):
+    """Max over ranks of a per-rank float (the slowest rank's time); identity
+    for one rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def percentiles(xs):
+    xs = np.asarray(xs, dtype=np.float64)
+    if xs.size == 0:
+        return {"p50": None, "p99": None}
+    return {"p50": float(np.percentile(xs, 50)), "p99": float(np.percentile(xs, 99))}
+
+
+# ---------------------------------------------------------------------------
+# Same-GPU comparator: the paper's unfused step structure (Section 4) in FP32
+# with cuFFT (through torch.fft) for steps 2, 4 and 6, a materialised complex
+# plane for steps 5-6, and this library's whitening and harmonic-sum stages.
+# ---------------------------------------------------------------------------
+def plain_fp32_path(fdas, plan, info, p, dev, stream):
+    import torch
+    Z, L, m, V, S, nb = info.Z, info.L, info.m, info.V, info.S, info.nb
+    bank = torch.empty(Z * L * 2, dtype=torch.float32, device=dev)
+    fdas.fdas_template_bank(plan, bank)  # natural order, 1/L folded in
+    # times L: torch's inverse FFT carries its own 1/L
+    bank = torch.view_as_complex(bank.view(Z, L, 2)) * float(L)
+    idx = (torch.arange(S, device=dev)[:, None] * V - m // 2
+           + torch.arange(L, device=dev)[None, :])
+    valid = (idx >= 0) & (idx < nb)
+    idx = idx.clamp(0, nb - 1)
+    zero = torch.zeros((), dtype=torch.complex64, device=dev)
+    white = torch.empty(nb * 2, dtype=torch.float32, device=dev)
+    plane = torch.empty(Z, nb, dtype=torch.float32, device=dev)
+    cands = torch.empty(info.max_cands * 16, dtype=torch.uint8, device=dev)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def step(x):
+        with torch.cuda.stream(stream):
+            X = torch.fft.rfft(x)[:nb].contiguous()                      # step 2
+            fdas.fdas_stage_whiten(plan, torch.view_as_real(X), white)
+            W = torch.view_as_complex(white.view(nb, 2))
+            seg = torch.where(valid, W[idx], zero)                        # step 3
+            F = torch.fft.fft(seg, dim=1)                                 # step 4
+            Y = bank[:, None, :] * F[None, :, :]                          # step 5 (Z, S, L)
+            y = torch.fft.ifft(Y, dim=2)                                  # step 6
+            pw = torch.abs(y[:, :, m // 2: m // 2 + V])                   # step 7: power,
+            pw.square_()                                                  # edge removal
+            plane.copy_(pw.view(Z, S * V)[:, :nb])
+            fdas.fdas_stage_harmsum(plan, plane, cands, count)
+        return count
+    return step
+
+
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle, timed on a bounded sample of one trial.
 # ---------------------------------------------------------------------------
@@ -215,7 +273,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -224,6 +282,10 @@ def main():
     ap.add_argument("--log2n", type=int, default=None,
                     help="smaller series length for profiling captures (not a bench value)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparator")
+    ap.add_argument("--plain-steps", type=int, default=10)
+    ap.add_argument("--segment", type=int, default=None,
+                    help="overlap-save segment length (default: the workload's 8192)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -258,6 +320,8 @@ def main():
                          for i in range(args.series - 1)]
     d_series = [torch.from_numpy(s).to(dev) for s in series]
 
+    if args.segment is not None:
+        p["L"] = args.segment
     stream = torch.cuda.Stream(dev)
     max_cands = 1 << 22
     plan = fdas.fdas_plan_create(p["N"], p["zmax"], p["dz"], p["m"], p["L"], p["nharm"],
@@ -274,24 +338,20 @@ def main():
             step(i)
     torch.cuda.synchronize(dev)
 
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with ClockSampler(local) as clk:
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
-        ev0.record(stream)
+        evs[0].record(stream)
         for i in range(args.steps):
             step(i)
-        ev1.record(stream)
+            evs[i + 1].record(stream)
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(evs[0].elapsed_time(evs[-1]), world, dev)
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     clocks = clk.summary()
     ms_per_step = ms / args.steps
     value = args.steps * world / (ms / 1e3)
@@ -317,6 +377,32 @@ def main():
         fdas.fdas_search_host(plan, h_series.data_ptr(), 1, h_out, h_cnt)
         d2h += 8 + 16 * int(min(h_cnt[0], max_cands))
     e2e_s = (time.perf_counter() - t0) / max(e2e_steps, 1)
+    e2e_lat = []
+    for i in range(e2e_steps):
+        t1 = time.perf_counter()
+        fdas.fdas_search_host(plan, h_series.data_ptr(), 1, h_out, h_cnt)
+        e2e_lat.append((time.perf_counter() - t1) * 1e3)
+
+    # the plain FP32 comparator on the same GPU, same series
+    plain = None
+    if not args.no_plain:
+        pstep = plain_fp32_path(fdas, plan, info, p, dev, stream)
+        for i in range(2):
+            pstep(d_series[i % len(d_series)])
+        torch.cuda.synchronize(dev)
+        pe = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        pe[0].record(stream)
+        for i in range(args.plain_steps):
+            pcnt = pstep(d_series[i % len(d_series)])
+        pe[1].record(stream)
+        torch.cuda.synchronize(dev)
+        pms = reduce_max(pe[0].elapsed_time(pe[1]), world, dev) / args.plain_steps
+        plain = {"value": world * 1e3 / pms, "unit": "trials/s", "ms_per_step": pms,
+                 "steps": args.plain_steps, "speedup": value / (world * 1e3 / pms),
+                 "candidates_last_step": int(pcnt.item()),
+                 "what": "unfused FP32 path: cuFFT (torch.fft) real FFT, segment and inverse FFTs, "
+                         "elementwise multiply into a materialised complex plane, power, edge trim; "
+                         "this library's whitening and harmonic sum"}
     fdas.fdas_plan_destroy(plan)
 
     peaks, peak_kind = load_peaks()
@@ -356,11 +442,14 @@ def main():
                        "l2": f"{len(d_series)} resident series cycled; each step writes a "
                              f"{Z * nb * 4 / 1e9:.2f} GB plane (> L2)"},
             "stage_ms": stage_ms, "candidates_last_step": n_cands,
+            "latency_ms": dict(percentiles(step_ms), what="per-trial device time, back to back"),
+            "vs_plain_fp32": plain,
             "roofline": roof,
             "clocks": clocks,
             "e2e": {"value": 1.0 / e2e_s if e2e_steps else None, "unit": "trials/s",
                     "h2d_bytes_per_step": 4 * N,
-                    "d2h_bytes_per_step": int(d2h / max(e2e_steps, 1))},
+                    "d2h_bytes_per_step": int(d2h / max(e2e_steps, 1)),
+                    "latency_ms": percentiles(e2e_lat)},
             "gpu_launches": int(info_kernels_per_trial() * args.steps),
             "peaks": {"source": peak_kind, "hbm_gbs": peaks.get("hbm_gbs")}}
     if rank == 0 and not args.no_cpu_baseline:
