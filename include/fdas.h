@@ -74,7 +74,7 @@ typedef struct {
  * response tau_z(d) of Section 2 for d = -m/2..m/2-1 in float64 on the GPU,
  * its length-L spectrum (float64 DFT, scaled by 1/L and rounded to float32),
  * and the float64-generated FFT twiddle tables.
- *   N: power of two, 2^12 <= N <= 2^24.  zmax >= 0, dz > 0, dz | zmax.
+ *   N: 2^a 3^b 5^c with a >= 12, 2^12 <= N <= 2^24.  zmax >= 0, dz > 0, dz | zmax.
  *   template_width m: multiple of 8, m >= 8.  segment L: 2048, 4096 or 8192, L >= 2m.
  *   nharm: 1, 2, 4, 8 or 16.  sigma > 0: Gaussian-equivalent threshold.
  *   max_cands >= 1: capacity of the candidate list per trial.
@@ -109,6 +109,24 @@ int fdas_search_host(fdas_plan* plan, const float* h_series, int32_t n_trials,
  * (entries past max_cands are dropped). */
 int fdas_search_device(fdas_plan* plan, const float* d_series, int32_t n_trials,
                        fdas_cand* d_out, int64_t* d_counts);
+
+/* Batches of DM trials of uneven length (series of different N).
+ * fdas_batch_create makes one plan for the longest series N_max (same
+ * arguments and limits as fdas_plan_create) whose workspaces and templates
+ * serve every trial; fdas_search_batch runs trial t of length N[t]
+ * (N[t] <= N_max, N[t] = 2^a 3^b 5^c with a >= 12) from d_series[t] (host
+ * array of device pointers, N[t] floats each) and, like fdas_search_device,
+ * enqueues the whole path asynchronously with unsorted candidates at
+ * d_out + t*max_cands and the exact count in d_counts[t] (device int64).
+ * The real-FFT geometry of each new length is built (and cached) on first
+ * use, which allocates its small twiddle tables. */
+typedef struct fdas_batch fdas_batch;
+int fdas_batch_create(fdas_batch** out, int64_t N_max, int32_t zmax, int32_t dz,
+                      int32_t template_width, int32_t segment, int32_t nharm, float sigma,
+                      int64_t max_cands, void* stream);
+int fdas_batch_destroy(fdas_batch* batch);
+int fdas_search_batch(fdas_batch* batch, const float* const* d_series, const int64_t* N,
+                      int32_t n_trials, fdas_cand* d_out, int64_t* d_counts);
 
 /* Test hook: copies the float32 power plane of the last trial processed,
  * Z x nb row-major by z (P[j*nb + r] = |A(r, z_j)|^2, Eq. 1), to d_plane. */

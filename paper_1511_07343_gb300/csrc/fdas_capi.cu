@@ -102,6 +102,55 @@ int run_trial(fdas_plan* p, const float* d_x, fdas_cand* d_out, unsigned long lo
   return launch_harmsum(p, p->plane, p->q4, d_out, d_count);
 }
 
+// N-dependent geometry of a plan: spectrum length, four-step split and the
+// segment count. N = 2^a 3^b 5^c with a >= 12 (the power-of-two path splits
+// M = N/2 into equal powers of two; other lengths use a balanced 2-3-5 split).
+int set_geometry(fdas_plan* p, int64_t N) {
+  if (N < (1 << 12) || N > (1 << 24) || N % 4096 != 0 || !is_235(N))
+    return set_error(FDAS_ERR_INVALID,
+                     "N must be 2^a 3^b 5^c with a >= 12 and 2^12 <= N <= 2^24");
+  p->N = N;
+  p->nb = N / 2;
+  p->M = N / 2;
+  const int h = log2i(p->M);
+  if (is_pow2(N)) {
+    p->M1 = 1 << ((h + 1) / 2);
+    p->M2 = 1 << (h / 2);
+  } else if (!split_235(p->M, &p->M1, &p->M2)) {
+    return set_error(FDAS_ERR_INVALID, "N has no supported four-step split");
+  }
+  p->h4 = (h + 1) / 2;
+  p->hN = (h + 1) / 2;
+  p->S = (int)((p->nb + p->V - 1) / p->V);
+  return FDAS_OK;
+}
+
+// the six N-dependent twiddle tables (float64-made) of the real FFT
+int alloc_geometry_tables(fdas_plan* p) {
+  int rc;
+  if ((rc = dalloc(p, &p->tw_M1, p->M1))) return rc;
+  if ((rc = dalloc(p, &p->tw_M2, p->M2))) return rc;
+  if ((rc = dalloc(p, &p->tw4_lo, (size_t)1 << p->h4))) return rc;
+  if ((rc = dalloc(p, &p->tw4_hi, (size_t)(p->M >> p->h4) + 1))) return rc;
+  if ((rc = dalloc(p, &p->twN_lo, (size_t)1 << p->hN))) return rc;
+  if ((rc = dalloc(p, &p->twN_hi, (size_t)(p->M >> p->hN) + 1))) return rc;
+  cudaStream_t s = p->stream;
+  if ((rc = launch_twiddles(p->tw_M1, p->M1, 1, p->M1, s))) return rc;
+  if ((rc = launch_twiddles(p->tw_M2, p->M2, 1, p->M2, s))) return rc;
+  if ((rc = launch_twiddles(p->tw4_lo, (int64_t)1 << p->h4, 1, p->M, s))) return rc;
+  if ((rc = launch_twiddles(p->tw4_hi, (p->M >> p->h4) + 1, (int64_t)1 << p->h4, p->M, s)))
+    return rc;
+  if ((rc = launch_twiddles(p->twN_lo, (int64_t)1 << p->hN, 1, p->N, s))) return rc;
+  return launch_twiddles(p->twN_hi, (p->M >> p->hN) + 1, (int64_t)1 << p->hN, p->N, s);
+}
+
+void free_geometry_tables(fdas_plan* p) {
+  void* ptrs[] = {p->tw_M1, p->tw_M2, p->tw4_lo, p->tw4_hi, p->twN_lo, p->twN_hi};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  p->tw_M1 = p->tw_M2 = p->tw4_lo = p->tw4_hi = p->twN_lo = p->twN_hi = nullptr;
+}
+
 bool cand_less(const fdas_cand& a, const fdas_cand& b) {
   if (a.h != b.h) return a.h < b.h;
   if (a.r_top != b.r_top) return a.r_top < b.r_top;
@@ -147,8 +196,6 @@ int fdas_plan_create(fdas_plan** out, int64_t N, int32_t zmax, int32_t dz, int32
                      int32_t L, int32_t nharm, float sigma, int64_t max_cands, void* stream) {
   if (!out) return set_error(FDAS_ERR_INVALID, "out is NULL");
   *out = nullptr;
-  if (!is_pow2(N) || N < (1 << 12) || N > (1 << 24))
-    return set_error(FDAS_ERR_INVALID, "N must be a power of two in [2^12, 2^24]");
   if (zmax < 0 || dz <= 0 || zmax % dz != 0)
     return set_error(FDAS_ERR_INVALID, "need zmax >= 0, dz > 0 and dz | zmax");
   if (m < 8 || (m & 7)) return set_error(FDAS_ERR_INVALID, "template width must be a multiple of 8");
@@ -159,32 +206,30 @@ int fdas_plan_create(fdas_plan** out, int64_t N, int32_t zmax, int32_t dz, int32
     return set_error(FDAS_ERR_INVALID, "nharm must be 1, 2, 4, 8 or 16");
   if (!(sigma > 0.f)) return set_error(FDAS_ERR_INVALID, "sigma must be > 0");
   if (max_cands < 1) return set_error(FDAS_ERR_INVALID, "max_cands must be >= 1");
-  if ((int64_t)(2 * (zmax / dz) + 1) * (N / 2) > (int64_t(1) << 40))
+  if (N < 0 || (int64_t)(2 * (zmax / dz) + 1) * (N / 2) > (int64_t(1) << 40))
     return set_error(FDAS_ERR_INVALID, "plane too large");
 
   fdas_plan* p = new fdas_plan();
-  p->N = N;
-  p->nb = N / 2;
-  p->M = N / 2;
-  const int h = log2i(p->M);
-  p->M1 = 1 << ((h + 1) / 2);
-  p->M2 = 1 << (h / 2);
   p->zmax = zmax;
   p->dz = dz;
   p->Z = 2 * (zmax / dz) + 1;
   p->m = m;
   p->L = L;
   p->V = L - m;
-  p->S = (int)((p->nb + p->V - 1) / p->V);
   p->nharm = nharm;
   p->n_levels = log2i(nharm) + 1;
   p->sigma = sigma;
   p->max_cands = max_cands;
   p->stream = (cudaStream_t)stream;
+  {
+    const int grc = set_geometry(p, N);
+    if (grc) {
+      delete p;
+      return grc;
+    }
+  }
   const double ptail = 0.5 * erfc((double)sigma / sqrt(2.0));
   for (int i = 0; i < p->n_levels; ++i) p->thr[i] = (float)gamma_q_inv_int(1 << i, ptail);
-  p->h4 = (h + 1) / 2;
-  p->hN = (h + 1) / 2;
 
   int rc = FDAS_OK;
 #define TRY(x)            \
@@ -195,12 +240,7 @@ int fdas_plan_create(fdas_plan** out, int64_t N, int32_t zmax, int32_t dz, int32
     }                     \
   } while (0)
   TRY(dalloc(p, &p->tw_L, L));
-  TRY(dalloc(p, &p->tw_M1, p->M1));
-  TRY(dalloc(p, &p->tw_M2, p->M2));
-  TRY(dalloc(p, &p->tw4_lo, (size_t)1 << p->h4));
-  TRY(dalloc(p, &p->tw4_hi, (size_t)(p->M >> p->h4) + 1));
-  TRY(dalloc(p, &p->twN_lo, (size_t)1 << p->hN));
-  TRY(dalloc(p, &p->twN_hi, (size_t)(p->M >> p->hN) + 1));
+  TRY(alloc_geometry_tables(p));
   TRY(dalloc(p, &p->taps, (size_t)p->Z * m));
   TRY(dalloc(p, &p->bank, (size_t)p->Z * L));
   TRY(dalloc(p, &p->series, (size_t)N));
@@ -216,12 +256,6 @@ int fdas_plan_create(fdas_plan** out, int64_t N, int32_t zmax, int32_t dz, int32
 
   cudaStream_t s = p->stream;
   TRY(launch_twiddles(p->tw_L, L, 1, L, s));
-  TRY(launch_twiddles(p->tw_M1, p->M1, 1, p->M1, s));
-  TRY(launch_twiddles(p->tw_M2, p->M2, 1, p->M2, s));
-  TRY(launch_twiddles(p->tw4_lo, (int64_t)1 << p->h4, 1, p->M, s));
-  TRY(launch_twiddles(p->tw4_hi, (p->M >> p->h4) + 1, (int64_t)1 << p->h4, p->M, s));
-  TRY(launch_twiddles(p->twN_lo, (int64_t)1 << p->hN, 1, p->N, s));
-  TRY(launch_twiddles(p->twN_hi, (p->M >> p->hN) + 1, (int64_t)1 << p->hN, p->N, s));
   TRY(launch_template_taps(p));
   TRY(launch_template_bank(p));
   TRY(cuda_check(cudaStreamSynchronize(s), "plan initialisation"));
@@ -374,6 +408,92 @@ int fdas_profile_trial(fdas_plan* p, const float* d_series, float* h_ms) {
 int fdas_host_fresnel(double x, double* C, double* S) {
   if (!C || !S) return set_error(FDAS_ERR_INVALID, "NULL argument");
   fresnel_host(x, C, S);
+  return FDAS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches of DM trials of uneven length: one plan's workspaces (sized for the
+// longest series) serve every trial; per length only the real-FFT geometry
+// and its twiddle tables differ, cached as lightweight views of the plan.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct fdas_batch {
+  fdas_plan* base = nullptr;
+  std::vector<fdas_plan*> views;
+};
+
+namespace {
+
+int batch_view(fdas_batch* b, int64_t N, fdas_plan** out) {
+  fdas_plan* base = b->base;
+  if (N == base->N) {
+    *out = base;
+    return FDAS_OK;
+  }
+  if (N > base->N) return set_error(FDAS_ERR_INVALID, "series longer than the batch's N_max");
+  for (fdas_plan* v : b->views)
+    if (v->N == N) {
+      *out = v;
+      return FDAS_OK;
+    }
+  fdas_plan* v = new fdas_plan(*base);  // shares the workspaces and templates
+  v->tw_M1 = v->tw_M2 = v->tw4_lo = v->tw4_hi = v->twN_lo = v->twN_hi = nullptr;
+  v->device_bytes = 0;
+  int rc = set_geometry(v, N);
+  if (!rc) rc = alloc_geometry_tables(v);
+  if (rc) {
+    free_geometry_tables(v);
+    delete v;
+    return rc;
+  }
+  b->views.push_back(v);
+  *out = v;
+  return FDAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdas_batch_create(fdas_batch** out, int64_t N_max, int32_t zmax, int32_t dz, int32_t m,
+                      int32_t L, int32_t nharm, float sigma, int64_t max_cands, void* stream) {
+  if (!out) return set_error(FDAS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  fdas_plan* base = nullptr;
+  int rc = fdas_plan_create(&base, N_max, zmax, dz, m, L, nharm, sigma, max_cands, stream);
+  if (rc) return rc;
+  fdas_batch* b = new fdas_batch();
+  b->base = base;
+  *out = b;
+  return FDAS_OK;
+}
+
+int fdas_batch_destroy(fdas_batch* b) {
+  if (!b) return FDAS_OK;
+  if (b->base && b->base->stream) cudaStreamSynchronize(b->base->stream);
+  for (fdas_plan* v : b->views) {
+    free_geometry_tables(v);
+    delete v;
+  }
+  fdas_plan_destroy(b->base);
+  delete b;
+  return FDAS_OK;
+}
+
+int fdas_search_batch(fdas_batch* b, const float* const* d_series, const int64_t* N,
+                      int32_t n_trials, fdas_cand* d_out, int64_t* d_counts) {
+  if (!b || !d_series || !N || n_trials < 0 || (n_trials > 0 && (!d_out || !d_counts)))
+    return set_error(FDAS_ERR_INVALID, "bad argument to fdas_search_batch");
+  for (int32_t t = 0; t < n_trials; ++t) {
+    if (!d_series[t]) return set_error(FDAS_ERR_INVALID, "NULL series in batch");
+    fdas_plan* v = nullptr;
+    int rc = batch_view(b, N[t], &v);
+    if (rc) return rc;
+    rc = run_trial(v, d_series[t], d_out + (size_t)t * v->max_cands,
+                   reinterpret_cast<unsigned long long*>(d_counts + t));
+    if (rc) return rc;
+  }
   return FDAS_OK;
 }
 

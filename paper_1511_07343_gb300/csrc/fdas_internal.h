@@ -63,8 +63,12 @@ int launch_template_taps(fdas_plan* p);
 int launch_template_bank(fdas_plan* p);
 void fresnel_host(double x, double* C, double* S);
 
-// fdas_spectrum.cu
+// fdas_spectrum.cu, fdas_spectrum_mixed.cu
 int launch_spectrum(fdas_plan* p, const float* d_series, float2* d_spec);
+int launch_unpack(fdas_plan* p, float2* d_spec);
+int launch_spectrum_mixed(fdas_plan* p, const float* d_series, float2* d_spec);
+bool is_235(int64_t x);
+bool split_235(int64_t M, int* M1, int* M2);
 int launch_whiten(fdas_plan* p, const float2* d_spec, float2* d_white);
 
 // fdas_correlate.cu

@@ -203,17 +203,25 @@ __global__ void __launch_bounds__(kWTile) k_whiten(const float2* __restrict__ X,
 
 }  // namespace
 
+int launch_unpack(fdas_plan* p, float2* d_spec) {
+  const int nt = 256;
+  k_unpack<<<(unsigned)((p->M + nt - 1) / nt), nt, 0, p->stream>>>(p->spec2, d_spec, p->M,
+                                                                     p->twN_lo, p->twN_hi, p->hN);
+  return cuda_check(cudaGetLastError(), "k_unpack");
+}
+
+static bool pow2_in(int x, int lo, int hi) { return x >= lo && x <= hi && (x & (x - 1)) == 0; }
+
 int launch_spectrum(fdas_plan* p, const float* d_series, float2* d_spec) {
+  if (!pow2_in(p->M1, 32, 4096) || !pow2_in(p->M2, 32, 4096))
+    return launch_spectrum_mixed(p, d_series, d_spec);
   const float2* z = reinterpret_cast<const float2*>(d_series);
   int rc = dispatch_cols(p, z, p->zbuf);
   if (rc) return rc;
   // the unpack reads bins k and M-k, so the packed FFT gets its own buffer
   rc = dispatch_rows(p, p->zbuf, p->spec2);
   if (rc) return rc;
-  const int nt = 256;
-  k_unpack<<<(unsigned)((p->M + nt - 1) / nt), nt, 0, p->stream>>>(p->spec2, d_spec, p->M,
-                                                                     p->twN_lo, p->twN_hi, p->hN);
-  return cuda_check(cudaGetLastError(), "k_unpack");
+  return launch_unpack(p, d_spec);
 }
 
 int launch_whiten(fdas_plan* p, const float2* d_spec, float2* d_white) {

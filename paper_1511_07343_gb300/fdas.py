@@ -60,6 +60,10 @@ _SIGS = {
     "fdas_search": [_P, _P, _I32, _P, _P],
     "fdas_search_host": [_P, _P, _I32, _P, _P],
     "fdas_search_device": [_P, _P, _I32, _P, _P],
+    "fdas_batch_create": [ctypes.POINTER(_P), _I64, _I32, _I32, _I32, _I32, _I32,
+                          ctypes.c_float, _I64, _P],
+    "fdas_batch_destroy": [_P],
+    "fdas_search_batch": [_P, _P, _P, _I32, _P, _P],
     "fdas_plane_debug": [_P, _P],
     "fdas_stage_spectrum": [_P, _P, _P],
     "fdas_stage_whiten": [_P, _P, _P],
@@ -153,6 +157,28 @@ def fdas_search_host(plan, h_series, n_trials, h_out, h_counts):
 def fdas_search_device(plan, d_series, n_trials, d_out, d_counts):
     _check(load().fdas_search_device(plan, _ptr(d_series), n_trials, _ptr(d_out),
                                      _ptr(d_counts)), "fdas_search_device")
+
+
+def fdas_batch_create(N_max, zmax, dz, template_width, segment, nharm, sigma=6.0,
+                      max_cands=1 << 20, stream=0):
+    batch = _P()
+    _check(load().fdas_batch_create(ctypes.byref(batch), N_max, zmax, dz, template_width, segment,
+                                    nharm, sigma, max_cands, _ptr(stream) or None),
+           "fdas_batch_create")
+    return batch.value
+
+
+def fdas_batch_destroy(batch):
+    _check(load().fdas_batch_destroy(batch), "fdas_batch_destroy")
+
+
+def fdas_search_batch(batch, d_series_list, N_list, d_out, d_counts):
+    n = len(d_series_list)
+    ptrs = (ctypes.c_void_p * n)(*[_ptr(x) for x in d_series_list])
+    lens = (ctypes.c_int64 * n)(*[int(v) for v in N_list])
+    _check(load().fdas_search_batch(batch, ctypes.cast(ptrs, ctypes.c_void_p),
+                                    ctypes.cast(lens, ctypes.c_void_p), n, _ptr(d_out),
+                                    _ptr(d_counts)), "fdas_search_batch")
 
 
 def fdas_plane_debug(plan, d_plane):

@@ -58,7 +58,7 @@ def test_host_fresnel_matches_scipy(lib, x):
 
 
 @pytest.mark.parametrize("args", [
-    dict(N=3000), dict(N=1 << 11), dict(N=1 << 25), dict(zmax=-2), dict(dz=0), dict(zmax=5, dz=2),
+    dict(N=3000), dict(N=1 << 11), dict(N=1 << 25), dict(N=7 * 4096), dict(N=3 * 2048), dict(zmax=-2), dict(dz=0), dict(zmax=5, dz=2),
     dict(m=7), dict(m=4), dict(L=1024), dict(L=2048, m=1100), dict(nharm=3), dict(nharm=32),
     dict(sigma=0.0), dict(max_cands=0)])
 def test_plan_create_rejects_bad_arguments(lib, args):
@@ -84,3 +84,15 @@ def test_null_arguments_are_rejected(lib):
     assert so.fdas_plan_get_info(None, None) == lib.FDAS_ERR_INVALID
     assert so.fdas_host_fresnel(1.0, None, None) == lib.FDAS_ERR_INVALID
     del ctypes
+
+
+@pytest.mark.parametrize("N", [3 * 4096, 5 * 4096, 15 * 4096, 45 * 4096, 3 << 21])
+def test_plan_create_accepts_235_lengths(lib, N):
+    """Uneven lengths 2^a 3^b 5^c (a >= 12) pass validation; on a machine
+    without a GPU creation then stops at the first device allocation."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("needs a machine without a GPU")
+    with pytest.raises(lib.FdasError) as e:
+        lib.fdas_plan_create(N, 20, 2, 64, 2048, 4, 6.0, 100)
+    assert e.value.status in (lib.FDAS_ERR_NOMEM, lib.FDAS_ERR_CUDA)
