@@ -186,6 +186,56 @@ def plain_fp32_path(fdas, plan, info, p, dev, stream):
 
 
 # ---------------------------------------------------------------------------
+# Serving: a stream of DM trials with zmax drawn from {50, 100, 200}, one in
+# ten at an uneven length from [2^21, 2^22] (snapped to 2^a 3^b 5^c), the rest
+# 2^23 samples; continuous batching over device-resident plans.
+# ---------------------------------------------------------------------------
+def serve_measure(dev, n_sat=48, n_poisson=60, rate=11.32, seed=5):
+    import torch
+    from paper_1511_07343_gb300.serve import Server
+    from synthetic import make_series, random_chirps, snap_235
+    rng = np.random.default_rng(seed)
+    pool = []
+    for i in range(8):
+        n = 1 << 23
+        if i == 7:
+            n = snap_235(np.exp(rng.uniform(np.log(2 ** 21), np.log(2 ** 22))))
+        chirps = random_chirps(rng, int(rng.integers(0, 4)), n, 200.0)
+        pool.append(make_series(n, 5000 + i, chirps, device=dev))
+    zs = [50, 100, 200]
+    with Server(n_max=1 << 23, n_slots=2, nharm=16, max_cands=1 << 20,
+                device=dev.index or 0) as srv:
+        # build every slot's plans once (device-resident afterwards)
+        warm = [srv.submit(pool[0], z) for z in zs for _ in range(2)]
+        for f in warm:
+            f.result()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        futs = [srv.submit(pool[i % 8], zs[int(rng.integers(0, 3))]) for i in range(n_sat)]
+        sat = [f.result() for f in futs]
+        t_sat = time.perf_counter() - t0
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_poisson))
+        t0 = time.perf_counter()
+        futs = []
+        for i, ta in enumerate(arrivals):
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            futs.append(srv.submit(pool[i % 8], zs[int(rng.integers(0, 3))]))
+        poi = [f.result() for f in futs]
+        t_poi = time.perf_counter() - t0
+        stats = dict(srv.stats)
+    lat = percentiles([r.latency_ms for r in poi])
+    return {"slots": 2, "zmax_classes": zs,
+            "saturating": {"trials": n_sat, "trials_per_s": n_sat / t_sat,
+                           "latency_ms": percentiles([r.latency_ms for r in sat])},
+            "poisson": {"rate_per_s": rate, "trials": n_poisson,
+                        "sustained_trials_per_s": n_poisson / t_poi, "latency_ms": lat},
+            "real_time_budget_trials_per_s": 6000 / 530.0, "stats": stats,
+            "what": "host series in, sorted candidates out; arrival to result, wall clock"}
+
+
+# ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle, timed on a bounded sample of one trial.
 # ---------------------------------------------------------------------------
 def oracle_trial_estimate(x, p, rows=3, hs_width=1 << 15):
@@ -284,6 +334,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparator")
     ap.add_argument("--plain-steps", type=int, default=10)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--segment", type=int, default=None,
                     help="overlap-save segment length (default: the workload's 8192)")
     args = ap.parse_args()
@@ -452,6 +503,8 @@ def main():
                     "latency_ms": percentiles(e2e_lat)},
             "gpu_launches": int(info_kernels_per_trial() * args.steps),
             "peaks": {"source": peak_kind, "hbm_gbs": peaks.get("hbm_gbs")}}
+    if rank == 0 and not args.no_serve and args.log2n is None:
+        line["serving"] = serve_measure(dev)
     if rank == 0 and not args.no_cpu_baseline:
         t_trial, sample = oracle_trial_estimate(series[0], p)
         line["cpu_baseline"] = {"value": 1.0 / t_trial, "unit": "trials/s", "cores": 1,

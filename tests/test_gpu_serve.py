@@ -1,0 +1,69 @@
+"""The serving loop: requests of mixed length and acceleration range, queued
+together and served by concurrent slots, give exactly the candidates that a
+standalone search of each one gives."""
+import numpy as np
+import pytest
+import torch
+
+from synthetic import Chirp, make_series
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+
+CLASSES = {20: (64, 2048), 40: (128, 2048)}
+
+
+def standalone(fd, x, zmax):
+    m, L = CLASSES[zmax]
+    n = x.shape[0]
+    stream = torch.cuda.current_stream(DEV).cuda_stream
+    plan = fd.fdas_plan_create(n, zmax, 2, m, L, 8, 6.0, 1 << 16, stream)
+    try:
+        info = fd.fdas_plan_get_info(plan)
+        d_x = torch.from_numpy(x).to(DEV)
+        out = np.zeros(info.max_cands, dtype=fd.CAND_DTYPE)
+        cnt = np.zeros(1, dtype=np.int64)
+        fd.fdas_search(plan, d_x, 1, out, cnt)
+        return out[:cnt[0]], int(cnt[0])
+    finally:
+        fd.fdas_plan_destroy(plan)
+
+
+def test_results_alone_equal_results_in_the_mix(gpu_lib):
+    from paper_1511_07343_gb300.serve import Server
+    fd = gpu_lib
+    lengths = [1 << 16, 3 << 14, 1 << 15, 5 << 13, 1 << 16, 3 << 14, 1 << 16, 1 << 15]
+    zs = [20, 40, 40, 20, 40, 20, 20, 40]
+    xs = [make_series(n, 70 + i, [Chirp(0.13 * n / 2 + 97 * i, 4.0 * (i % 3) - 3, 9.0, 0.1 * i, 4)])
+          for i, n in enumerate(lengths)]
+    with Server(n_max=1 << 16, n_slots=3, classes=CLASSES, nharm=8, max_cands=1 << 16) as srv:
+        futs = [srv.submit(x, z) for x, z in zip(xs, zs)]
+        res = [f.result(timeout=300) for f in futs]
+        assert srv.stats["admitted"] == len(xs)
+    for x, z, r in zip(xs, zs, res):
+        ref, cnt = standalone(fd, x, z)
+        assert r.count == cnt
+        assert cnt > 0
+        assert r.candidates.tobytes() == np.sort(ref, order=["h", "r_top", "z_idx"]).tobytes()
+        assert r.latency_ms > 0
+
+
+def test_memory_budget_limits_plans(gpu_lib):
+    """With room for a single plan, slots take turns with it (evicting and
+    rebuilding per class) and every request still completes."""
+    from paper_1511_07343_gb300.serve import Server
+    srv = Server(n_max=1 << 15, n_slots=2, classes=CLASSES, nharm=4, max_cands=1 << 14,
+                 hbm_budget=1)
+    with pytest.raises(ValueError):
+        srv.submit(np.zeros(1 << 15, dtype=np.float32), 20)
+    srv.close()
+    one = Server(n_max=1 << 15, n_slots=2, classes=CLASSES, nharm=4, max_cands=1 << 14)
+    budget = max(one._footprint(z) for z in CLASSES)
+    one.close()
+    with Server(n_max=1 << 15, n_slots=2, classes=CLASSES, nharm=4, max_cands=1 << 14,
+                hbm_budget=budget) as srv:
+        xs = [make_series(1 << 15, 200 + i, [Chirp(3000.0 + 10 * i, 2.0, 12.0, 0.0, 2)])
+              for i in range(6)]
+        futs = [srv.submit(x, (20, 40)[i % 2]) for i, x in enumerate(xs)]
+        res = [f.result(timeout=300) for f in futs]
+    assert all(r.count > 0 for r in res)
