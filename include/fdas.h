@@ -156,6 +156,29 @@ int fdas_template_bank(fdas_plan* plan, float* d_bank);
  * (steps 5-7), harmonic sum + threshold + compaction. */
 int fdas_profile_trial(fdas_plan* plan, const float* d_series, float* h_ms);
 
+/* Correlation modes (steps 5-7 of Section 4, Eq. 1). */
+enum fdas_corr_mode {
+  FDAS_CORR_FFT = 0,       /* overlap-save FFT correlation, float32 (default) */
+  FDAS_CORR_GEMM_BF16 = 1, /* tensor-core GEMM, bf16 hi/lo split, float32 accumulation */
+  FDAS_CORR_GEMM_FP16 = 2  /* tensor-core GEMM, fp16 hi/lo split, float32 accumulation */
+};
+
+/* Selects how the plan computes the power plane of Eq. 1. The GEMM modes
+ * evaluate Eq. 1 directly as a dense contraction: for each block of 512
+ * consecutive bins, (2Z x 6m template matrix) x (6m x 512 Hankel-blocked
+ * spectrum) on the tcgen05 tensor cores. Each float32 operand is split into
+ * a 16-bit hi part and a lo part (fp16: lo scaled by 2^11 to stay normal);
+ * the products hi*hi + hi*lo + lo*hi are summed in float32, so the plane
+ * carries about 16 (bf16) or 22 (fp16) significant bits. The whitened
+ * spectrum must stay below 65504 in magnitude for the fp16 mode. Both modes
+ * feed the same harmonic sum and threshold. The left factor is built from the
+ * plan's float64 taps when the mode is selected and held until the plan is
+ * destroyed (2Z rounded up to 128 rows x 6m x 2 bytes).
+ *   mode: an fdas_corr_mode. The GEMM modes need m % 32 == 0 and m <= 768.
+ * A bounded device wait that gives up makes the next fdas_search return
+ * FDAS_ERR_TIMEOUT. */
+int fdas_plan_set_correlation(fdas_plan* plan, int32_t mode);
+
 /* Real FFT of one series without a plan and without allocating device memory.
  * The paper has no counterpart; this exists for callers that must not
  * allocate device memory (for example a real-time loop with a fixed device

@@ -83,11 +83,14 @@ void free_plan(fdas_plan* p) {
   if (!p) return;
   void* ptrs[] = {p->tw_L, p->tw_M1, p->tw_M2, p->tw4_lo, p->tw4_hi, p->twN_lo, p->twN_hi,
                   p->taps, p->bank, p->series, p->zbuf, p->spec, p->spec2, p->white, p->seg,
-                  p->plane, p->q4, p->cands, p->count};
+                  p->plane, p->q4, p->cands, p->count, p->gbank, p->gstatus};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
 }
+
+int launch_plane(fdas_plan* p, float* d_plane, float* d_q4, fdas_cand* d_out,
+                 unsigned long long* d_count);
 
 // The path for one trial; the plane goes to p->plane, candidates to d_out.
 int run_trial(fdas_plan* p, const float* d_x, fdas_cand* d_out, unsigned long long* d_count) {
@@ -97,9 +100,36 @@ int run_trial(fdas_plan* p, const float* d_x, fdas_cand* d_out, unsigned long lo
     return rc;
   if ((rc = launch_spectrum(p, d_x, p->spec))) return rc;
   if ((rc = launch_whiten(p, p->spec, p->white))) return rc;
-  if ((rc = launch_segments(p, p->white))) return rc;
-  if ((rc = launch_correlate(p, p->plane, p->q4, d_out, d_count))) return rc;
+  if ((rc = launch_plane(p, p->plane, p->q4, d_out, d_count))) return rc;
   return launch_harmsum(p, p->plane, p->q4, d_out, d_count);
+}
+
+// Steps 3-7 for the plan's correlation mode: the plane, its 4-bin maxima and
+// the h = 1 candidates (when d_q4 is given).
+int launch_plane(fdas_plan* p, float* d_plane, float* d_q4, fdas_cand* d_out,
+                 unsigned long long* d_count) {
+  int rc;
+  if (p->corr_mode == FDAS_CORR_FFT) {
+    if ((rc = launch_segments(p, p->white))) return rc;
+    return launch_correlate(p, d_plane, d_q4, d_out, d_count);
+  }
+  if ((rc = launch_gemm_correlate(p, d_plane))) return rc;
+  return d_q4 ? launch_pool4(p, d_plane, d_q4, d_out, d_count) : FDAS_OK;
+}
+
+// Status word of the tensor-core kernel's bounded waits (0 when none gave up).
+int gemm_status(fdas_plan* p) {
+  if (p->corr_mode == FDAS_CORR_FFT) return FDAS_OK;
+  int st = 0;
+  int rc = cuda_check(cudaMemcpyAsync(&st, p->gstatus, sizeof(int), cudaMemcpyDeviceToHost,
+                                      p->stream), "copy status");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(p->stream), "sync status");
+  if (rc) return rc;
+  if (st) {
+    cudaMemsetAsync(p->gstatus, 0, sizeof(int), p->stream);
+    return set_error(FDAS_ERR_TIMEOUT, "a bounded wait of the tensor-core correlation gave up");
+  }
+  return FDAS_OK;
 }
 
 // N-dependent geometry of a plan: spectrum length, four-step split and the
@@ -169,6 +199,7 @@ int search_impl(fdas_plan* p, const float* d_series, int32_t n_trials, fdas_cand
                     "copy count");
     if (rc) return rc;
     if ((rc = cuda_check(cudaStreamSynchronize(p->stream), "sync count"))) return rc;
+    if ((rc = gemm_status(p))) return rc;
     h_counts[t] = (int64_t)cnt;
     const int64_t keep = std::min<int64_t>((int64_t)cnt, p->max_cands);
     if ((int64_t)cnt > p->max_cands) overflow = true;
@@ -350,9 +381,40 @@ int fdas_stage_whiten(fdas_plan* p, const float* d_spectrum, float* d_white) {
 
 int fdas_stage_plane(fdas_plan* p, const float* d_white, float* d_plane) {
   if (!p || !d_white || !d_plane) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  if (p->corr_mode != FDAS_CORR_FFT) {
+    // the tensor-core kernel reads the plan's whitened spectrum
+    int rc = cuda_check(cudaMemcpyAsync(p->white, d_white, sizeof(float2) * (size_t)p->nb,
+                                        cudaMemcpyDeviceToDevice, p->stream), "copy spectrum");
+    if (rc) return rc;
+    if ((rc = launch_gemm_correlate(p, d_plane))) return rc;
+    return gemm_status(p);
+  }
   int rc = launch_segments(p, reinterpret_cast<const float2*>(d_white));
   if (rc) return rc;
   return launch_correlate(p, d_plane, nullptr, nullptr, nullptr);
+}
+
+int fdas_plan_set_correlation(fdas_plan* p, int32_t mode) {
+  if (!p) return set_error(FDAS_ERR_INVALID, "NULL plan");
+  if (mode != FDAS_CORR_FFT && mode != FDAS_CORR_GEMM_BF16 && mode != FDAS_CORR_GEMM_FP16)
+    return set_error(FDAS_ERR_INVALID, "unknown correlation mode");
+  if (mode == FDAS_CORR_FFT) {
+    p->corr_mode = mode;
+    return FDAS_OK;
+  }
+  int rc = gemm_check_shape(p);
+  if (rc) return rc;
+  if (!p->gbank && (rc = dalloc(p, &p->gbank, gemm_bank_elems(p)))) return rc;
+  if (!p->gstatus && (rc = dalloc(p, &p->gstatus, 1))) return rc;
+  if ((rc = cuda_check(cudaMemsetAsync(p->gstatus, 0, sizeof(int), p->stream), "memset status")))
+    return rc;
+  const int old = p->corr_mode;
+  p->corr_mode = mode;
+  if ((rc = launch_gemm_bank(p))) {
+    p->corr_mode = old;
+    return rc;
+  }
+  return cuda_check(cudaStreamSynchronize(p->stream), "template matrix");
 }
 
 int fdas_stage_harmsum(fdas_plan* p, const float* d_plane, fdas_cand* d_out, int64_t* d_count) {
@@ -392,9 +454,11 @@ int fdas_profile_trial(fdas_plan* p, const float* d_series, float* h_ms) {
   if (!rc) rc = cuda_check(cudaEventRecord(ev[1], p->stream), "event");
   if (!rc) rc = launch_whiten(p, p->spec, p->white);
   if (!rc) rc = cuda_check(cudaEventRecord(ev[2], p->stream), "event");
-  if (!rc) rc = launch_segments(p, p->white);
+  if (!rc && p->corr_mode == FDAS_CORR_FFT) rc = launch_segments(p, p->white);
   if (!rc) rc = cuda_check(cudaEventRecord(ev[3], p->stream), "event");
-  if (!rc) rc = launch_correlate(p, p->plane, p->q4, p->cands, p->count);
+  if (!rc && p->corr_mode == FDAS_CORR_FFT)
+    rc = launch_correlate(p, p->plane, p->q4, p->cands, p->count);
+  if (!rc && p->corr_mode != FDAS_CORR_FFT) rc = launch_plane(p, p->plane, p->q4, p->cands, p->count);
   if (!rc) rc = cuda_check(cudaEventRecord(ev[4], p->stream), "event");
   if (!rc) rc = launch_harmsum(p, p->plane, p->q4, p->cands, p->count);
   if (!rc) rc = cuda_check(cudaEventRecord(ev[5], p->stream), "event");

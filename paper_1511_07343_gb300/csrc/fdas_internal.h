@@ -46,6 +46,11 @@ struct fdas_plan {
   fdas_cand* cands = nullptr;  // max_cands
   unsigned long long* count = nullptr;
 
+  // tensor-core correlation (precision variant); corr_mode = FDAS_CORR_*
+  int corr_mode = 0;
+  uint16_t* gbank = nullptr;   // 16-bit left factor, pre-tiled (see fdas_gemm.cu)
+  int* gstatus = nullptr;      // device status word of the bounded waits
+
   int64_t device_bytes = 0;
   int corr_ctas_per_sm = 0;  // launch shape of the correlation kernel (last launch)
   int corr_grid = 0;
@@ -76,6 +81,12 @@ int launch_segments(fdas_plan* p, const float2* d_white);
 int launch_bank_natural(fdas_plan* p, float2* d_out);
 int launch_correlate(fdas_plan* p, float* d_plane, float* d_q4, fdas_cand* d_cands,
                      unsigned long long* d_count);
+
+// fdas_gemm.cu
+size_t gemm_bank_elems(const fdas_plan* p);
+int gemm_check_shape(const fdas_plan* p);
+int launch_gemm_bank(fdas_plan* p);
+int launch_gemm_correlate(fdas_plan* p, float* d_plane);
 
 // fdas_harmsum.cu
 int launch_pool4(fdas_plan* p, const float* d_plane, float* d_q4, fdas_cand* d_out,

@@ -21,6 +21,9 @@ FDAS_ERR_NOMEM = -2
 FDAS_ERR_CUDA = -3
 FDAS_ERR_TIMEOUT = -4
 FDAS_ERR_OVERFLOW = -5
+FDAS_CORR_FFT = 0
+FDAS_CORR_GEMM_BF16 = 1
+FDAS_CORR_GEMM_FP16 = 2
 
 
 class fdas_cand(ctypes.Structure):
@@ -73,6 +76,7 @@ _SIGS = {
     "fdas_template_bank": [_P, _P],
     "fdas_profile_trial": [_P, _P, _P],
     "fdas_spectrum_noalloc": [_P, _I64, _P, _P],
+    "fdas_plan_set_correlation": [_P, _I32],
     "fdas_host_fresnel": [ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_double)],
 }
@@ -215,6 +219,10 @@ def fdas_profile_trial(plan, d_series):
     ms = np.zeros(5, dtype=np.float32)
     _check(load().fdas_profile_trial(plan, _ptr(d_series), ms.ctypes.data), "fdas_profile_trial")
     return ms
+
+
+def fdas_plan_set_correlation(plan, mode):
+    _check(load().fdas_plan_set_correlation(plan, mode), "fdas_plan_set_correlation")
 
 
 def fdas_spectrum_noalloc(d_series, N, d_spectrum, stream=0):
