@@ -236,6 +236,76 @@ def serve_measure(dev, n_sat=48, n_poisson=60, rate=11.32, seed=5):
 
 
 # ---------------------------------------------------------------------------
+# Precision variants: the correlation of Eq. 1 as a tensor-core GEMM with
+# hi/lo-split bf16 or fp16 operands (float32 accumulation), same workload.
+# Agreement is measured against the float32 FFT path on the same series (the
+# error against the FP64 oracle comes from the GPU parity tests).
+# ---------------------------------------------------------------------------
+def precision_variants(fdas, p, dev, stream, d_series, ref_plane, ref_keys, steps, peaks,
+                       peak_kind):
+    import torch
+    out = {}
+    max_cands = 1 << 22
+    for name, mode in (("bf16_hilo", fdas.FDAS_CORR_GEMM_BF16), ("fp16_hilo", fdas.FDAS_CORR_GEMM_FP16)):
+        plan = fdas.fdas_plan_create(p["N"], p["zmax"], p["dz"], p["m"], p["L"], p["nharm"],
+                                     p["sigma"], max_cands, stream.cuda_stream)
+        try:
+            fdas.fdas_plan_set_correlation(plan, mode)
+            info = fdas.fdas_plan_get_info(plan)
+            d_out = torch.empty(max_cands * 16, dtype=torch.uint8, device=dev)
+            d_cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+            with torch.cuda.stream(stream):
+                for i in range(3):
+                    fdas.fdas_search_device(plan, d_series[i % len(d_series)], 1, d_out, d_cnt)
+            torch.cuda.synchronize(dev)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            for i in range(steps):
+                fdas.fdas_search_device(plan, d_series[i % len(d_series)], 1, d_out, d_cnt)
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            ms = ev[0].elapsed_time(ev[1]) / steps
+            prof = np.stack([fdas.fdas_profile_trial(plan, d_series[0]) for _ in range(3)])
+            corr_ms = float(np.median(prof[:, 3]))
+            # agreement with the float32 path on series 0
+            h_out = np.zeros(max_cands, dtype=fdas.CAND_DTYPE)
+            h_cnt = np.zeros(1, dtype=np.int64)
+            fdas.fdas_search(plan, d_series[0], 1, h_out, h_cnt)
+            keys = {(int(c["r_top"]), int(c["z_idx"]), int(c["h"]))
+                    for c in h_out[:min(int(h_cnt[0]), max_cands)]}
+            plane = torch.empty(info.Z * info.nb, dtype=torch.float32, device=dev)
+            fdas.fdas_plane_debug(plan, plane)
+            torch.cuda.synchronize(dev)
+            rel = float(((plane - ref_plane).abs() / ref_plane.clamp(min=1.0)).max().item())
+            del plane
+        finally:
+            fdas.fdas_plan_destroy(plan)
+        Z, nb, m = info.Z, info.nb, info.m
+        rows = -(-2 * Z // 128) * 128
+        flops = 2.0 * 2 * Z * nb * 6 * m           # useful: 2Z rows x 6m x nb
+        issued = 2.0 * rows * nb * 6 * m           # rows padded to the 128-row tile
+        # the kernel is timed alone between events: the burst figure
+        peak = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])
+        ach = flops / (corr_ms / 1e3) / 1e12
+        out[name] = {
+            "value": 1e3 / ms, "unit": "trials/s", "ms_per_step": ms, "steps": steps,
+            "stage_ms": {s: float(np.median(prof[:, i])) for i, s in
+                         enumerate(["spectrum", "whiten", "segments", "correlate", "harmsum"])},
+            "roofline": {"kernel": "k_gemm_correlate", "bound": "tensor", "achieved": ach,
+                         "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "issued_frac": issued / (corr_ms / 1e3) / 1e12 / peak,
+                         "peak_source": f"{peak_kind} bf16_tflops (fp16 dense rate = bf16)",
+                         "algorithmic": f"2 x 2Z x nb x 6m = {flops:.3e} flop per launch "
+                                        f"(3 hi/lo products, complex as 2 real rows)"},
+            "vs_fp32_path": {"plane_max_rel": rel, "what": "max |dP|/max(P,1) over the whole "
+                             "plane against the float32 FFT path, same series",
+                             "candidates": len(keys), "fp32_candidates": len(ref_keys),
+                             "common": len(keys & ref_keys)},
+        }
+    return out
+
+
+# ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle, timed on a bounded sample of one trial.
 # ---------------------------------------------------------------------------
 def oracle_trial_estimate(x, p, rows=3, hs_width=1 << 15):
@@ -335,6 +405,10 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparator")
     ap.add_argument("--plain-steps", type=int, default=10)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the tensor-core precision variants")
+    ap.add_argument("--corr", choices=["fft", "bf16", "fp16"], default="fft",
+                    help="correlation mode of the timed path (profiling; default fft)")
     ap.add_argument("--segment", type=int, default=None,
                     help="overlap-save segment length (default: the workload's 8192)")
     args = ap.parse_args()
@@ -377,6 +451,8 @@ def main():
     max_cands = 1 << 22
     plan = fdas.fdas_plan_create(p["N"], p["zmax"], p["dz"], p["m"], p["L"], p["nharm"],
                                  p["sigma"], max_cands, stream.cuda_stream)
+    if args.corr != "fft":
+        fdas.fdas_plan_set_correlation(plan, {"bf16": 1, "fp16": 2}[args.corr])
     info = fdas.fdas_plan_get_info(plan)
     d_out = torch.empty(max_cands * 16, dtype=torch.uint8, device=dev)
     d_cnt = torch.zeros(1, dtype=torch.int64, device=dev)
@@ -454,13 +530,30 @@ def main():
                  "what": "unfused FP32 path: cuFFT (torch.fft) real FFT, segment and inverse FFTs, "
                          "elementwise multiply into a materialised complex plane, power, edge trim; "
                          "this library's whitening and harmonic sum"}
+    variants_ref = None
+    if rank == 0 and not args.no_variants and args.corr == "fft":
+        ref_plane = torch.empty(info.Z * info.nb, dtype=torch.float32, device=dev)
+        fdas.fdas_search(plan, d_series[0], 1, h_out, h_cnt)
+        fdas.fdas_plane_debug(plan, ref_plane)
+        torch.cuda.synchronize(dev)
+        ref_keys = {(int(c["r_top"]), int(c["z_idx"]), int(c["h"]))
+                    for c in h_out[:min(int(h_cnt[0]), max_cands)]}
+        variants_ref = (ref_plane, ref_keys)
     fdas.fdas_plan_destroy(plan)
 
     peaks, peak_kind = load_peaks()
     # dominant kernel and its roofline
     dom = max(stage_ms, key=stage_ms.get)
     N, Z, L, m, V, S, nb = p["N"], info.Z, info.L, info.m, info.V, info.S, info.nb
-    if dom == "correlate":
+    if dom == "correlate" and args.corr != "fft":
+        flops = 2.0 * 2 * Z * nb * 6 * m
+        peak = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])
+        achieved = flops / (stage_ms[dom] / 1e3) / 1e12
+        roof = {"kernel": "k_gemm_correlate", "bound": "tensor", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{peak_kind} bf16_tflops",
+                "algorithmic": f"2 x 2Z x nb x 6m = {flops:.3e} flop per launch"}
+    elif dom == "correlate":
         flops = S * Z * (5.0 * L * math.log2(L) + 6.0 * L + 3.0 * V)
         sm_max = peaks.get("sm_max_mhz", 2070.0)
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
@@ -503,6 +596,12 @@ def main():
                     "latency_ms": percentiles(e2e_lat)},
             "gpu_launches": int(info_kernels_per_trial() * args.steps),
             "peaks": {"source": peak_kind, "hbm_gbs": peaks.get("hbm_gbs")}}
+    if variants_ref is not None:
+        line["precision_variants"] = precision_variants(
+            fdas, p, dev, stream, d_series, variants_ref[0], variants_ref[1], 10, peaks, peak_kind)
+        del variants_ref
+    if args.corr != "fft":
+        line["config"]["correlation"] = args.corr + "_hilo_tensor_core"
     if rank == 0 and not args.no_serve and args.log2n is None:
         line["serving"] = serve_measure(dev)
     if rank == 0 and not args.no_cpu_baseline:

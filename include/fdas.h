@@ -155,6 +155,9 @@ int fdas_template_bank(fdas_plan* plan, float* d_bank);
  * for: spectrum (step 2), whitening, segment FFTs (steps 3-4), correlation
  * (steps 5-7), harmonic sum + threshold + compaction. */
 int fdas_profile_trial(fdas_plan* plan, const float* d_series, float* h_ms);
+/* (In the tensor-core correlation modes the segment entry is 0, the
+ * correlation entry is the GEMM kernel alone, and the harmonic-sum entry
+ * includes the 4-bin maxima and h = 1 threshold kernel.) */
 
 /* Correlation modes (steps 5-7 of Section 4, Eq. 1). */
 enum fdas_corr_mode {

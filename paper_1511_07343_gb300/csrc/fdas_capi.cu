@@ -454,12 +454,15 @@ int fdas_profile_trial(fdas_plan* p, const float* d_series, float* h_ms) {
   if (!rc) rc = cuda_check(cudaEventRecord(ev[1], p->stream), "event");
   if (!rc) rc = launch_whiten(p, p->spec, p->white);
   if (!rc) rc = cuda_check(cudaEventRecord(ev[2], p->stream), "event");
-  if (!rc && p->corr_mode == FDAS_CORR_FFT) rc = launch_segments(p, p->white);
+  // the tensor-core modes have no segment FFTs; their 4-bin maxima and h = 1
+  // threshold (a separate kernel there) count as harmonic-sum time
+  const bool fft = p->corr_mode == FDAS_CORR_FFT;
+  if (!rc && fft) rc = launch_segments(p, p->white);
   if (!rc) rc = cuda_check(cudaEventRecord(ev[3], p->stream), "event");
-  if (!rc && p->corr_mode == FDAS_CORR_FFT)
-    rc = launch_correlate(p, p->plane, p->q4, p->cands, p->count);
-  if (!rc && p->corr_mode != FDAS_CORR_FFT) rc = launch_plane(p, p->plane, p->q4, p->cands, p->count);
+  if (!rc) rc = fft ? launch_correlate(p, p->plane, p->q4, p->cands, p->count)
+                    : launch_gemm_correlate(p, p->plane);
   if (!rc) rc = cuda_check(cudaEventRecord(ev[4], p->stream), "event");
+  if (!rc && !fft) rc = launch_pool4(p, p->plane, p->q4, p->cands, p->count);
   if (!rc) rc = launch_harmsum(p, p->plane, p->q4, p->cands, p->count);
   if (!rc) rc = cuda_check(cudaEventRecord(ev[5], p->stream), "event");
   if (!rc) rc = cuda_check(cudaEventSynchronize(ev[5]), "event sync");
