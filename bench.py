@@ -236,6 +236,71 @@ def serve_measure(dev, n_sat=48, n_poisson=60, rate=11.32, seed=5):
 
 
 # ---------------------------------------------------------------------------
+# Batched uneven trials: 256 DM trials, N log-uniform in [2^20, 2^23] snapped
+# to 2^a 3^b 5^c, 0-3 accelerated signals each, zmax = 200; one autotuned
+# batch (segment length timed on a probe), each batch one CUDA graph launch.
+# ---------------------------------------------------------------------------
+def batch_measure(fdas, dev, n_trials=256, reps=2, seed=3):
+    import torch
+    from synthetic import make_series, random_chirps, snap_235
+    rng = np.random.default_rng(seed)
+    lens = [snap_235(math.exp(rng.uniform(math.log(2 ** 20), math.log(2 ** 23))))
+            for _ in range(n_trials)]
+    # 8 distinct series of 2^23 samples; trial t takes a prefix of one of them
+    base = [torch.from_numpy(make_series(1 << 23, 9000 + i,
+                                         random_chirps(rng, int(rng.integers(0, 4)),
+                                                       1 << 20, 200.0),
+                                         device=dev)).to(dev) for i in range(8)]
+    xs = [base[t % 8][:lens[t]] for t in range(n_trials)]
+    stream = torch.cuda.Stream(dev)
+    maxc = 1 << 16
+    t0 = time.perf_counter()
+    batch = fdas.fdas_batch_create_tuned(1 << 23, 200, 2, 512, 16, 6.0, maxc, None,
+                                         stream.cuda_stream)
+    tune_s = time.perf_counter() - t0
+    try:
+        info = fdas.fdas_batch_get_info(batch)
+        d_out = torch.empty(n_trials * maxc * 16, dtype=torch.uint8, device=dev)
+        d_cnt = torch.zeros(n_trials, dtype=torch.int64, device=dev)
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(stream):
+            fdas.fdas_search_batch(batch, xs, lens, d_out, d_cnt)   # views + capture
+        torch.cuda.synchronize(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(reps):
+                fdas.fdas_search_batch(batch, xs, lens, d_out, d_cnt)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        g_ms = ev[0].elapsed_time(ev[1]) / reps
+        cands = int(d_cnt.sum().item())
+        fdas.fdas_batch_set_graphs(batch, 0)
+        ev[0].record(stream)
+        with torch.cuda.stream(stream):
+            fdas.fdas_search_batch(batch, xs, lens, d_out, d_cnt)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        d_ms = ev[0].elapsed_time(ev[1])
+        info = fdas.fdas_batch_get_info(batch)
+    finally:
+        fdas.fdas_batch_destroy(batch)
+    return {"trials": n_trials, "N_min": min(lens), "N_max": max(lens),
+            "distinct_N": len(set(lens)), "zmax": 200, "template_width": 512,
+            "segment": info.segment,
+            "tuner": {"segments": list(info.tuned_segment[:info.n_tuned]),
+                      "trial_ms_at_N_max": [round(v, 4) for v in info.tuned_ms[:info.n_tuned]],
+                      "seconds": tune_s},
+            "graph": {"value": n_trials * 1e3 / g_ms, "unit": "trials/s", "ms_per_batch": g_ms,
+                      "batches": reps, "builds": info.graph_builds,
+                      "launches": info.graph_launches},
+            "direct": {"value": n_trials * 1e3 / d_ms, "unit": "trials/s", "ms_per_batch": d_ms},
+            "candidates_per_batch": cands,
+            "what": "series resident in HBM; one fdas_search_batch = one graph launch of all "
+                    "trials' kernels"}
+
+
+# ---------------------------------------------------------------------------
 # Precision variants: the correlation of Eq. 1 as a tensor-core GEMM with
 # hi/lo-split bf16 or fp16 operands (float32 accumulation), same workload.
 # Agreement is measured against the float32 FFT path on the same series (the
@@ -405,6 +470,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparator")
     ap.add_argument("--plain-steps", type=int, default=10)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched uneven-trial measurement")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the tensor-core precision variants")
     ap.add_argument("--corr", choices=["fft", "bf16", "fp16"], default="fft",
@@ -600,6 +667,8 @@ def main():
         line["precision_variants"] = precision_variants(
             fdas, p, dev, stream, d_series, variants_ref[0], variants_ref[1], 10, peaks, peak_kind)
         del variants_ref
+    if rank == 0 and not args.no_batch and args.log2n is None:
+        line["batch_uneven"] = batch_measure(fdas, dev)
     if args.corr != "fft":
         line["config"]["correlation"] = args.corr + "_hilo_tensor_core"
     if rank == 0 and not args.no_serve and args.log2n is None:

@@ -127,6 +127,38 @@ int fdas_batch_create(fdas_batch** out, int64_t N_max, int32_t zmax, int32_t dz,
 int fdas_batch_destroy(fdas_batch* batch);
 int fdas_search_batch(fdas_batch* batch, const float* const* d_series, const int64_t* N,
                       int32_t n_trials, fdas_cand* d_out, int64_t* d_counts);
+/* On a stream other than the legacy default stream, fdas_search_batch
+ * captures the whole batch (every trial's kernels and count resets, in
+ * order) into one CUDA graph and launches it as a single graph launch. The
+ * executable graph is kept: a later call with the same series pointers,
+ * lengths and output pointers replays it without capturing; other
+ * arguments re-capture and update it in place when the topology allows.
+ * fdas_batch_set_graphs(batch, 0) launches the kernels directly instead. */
+int fdas_batch_set_graphs(fdas_batch* batch, int32_t enable);
+
+/* Autotuned batch: times one trial of every segment length L in
+ * {2048, 4096, 8192} with L >= 2m on a probe series of N_max samples
+ * (d_probe, device; NULL = seeded Gaussian white noise made on the device),
+ * each on a fresh plan (median of 3 after a warm-up), and creates the batch
+ * with the fastest. L sets the segment FFT size, the number of segments and
+ * the correlation kernel's occupancy; the plane is the same up to float32
+ * rounding for every L. Other arguments as fdas_batch_create. */
+int fdas_batch_create_tuned(fdas_batch** out, int64_t N_max, int32_t zmax, int32_t dz,
+                            int32_t template_width, int32_t nharm, float sigma,
+                            int64_t max_cands, const float* d_probe, void* stream);
+
+typedef struct {
+  int64_t N_max;
+  int32_t segment;          /* L in use */
+  int32_t n_lengths;        /* distinct series lengths with a geometry */
+  int32_t graphs;           /* 1 when batches run as captured CUDA graphs */
+  int32_t n_tuned;          /* segment lengths the autotuner timed (0: not tuned) */
+  int64_t graph_builds;     /* captures made */
+  int64_t graph_launches;   /* graph launches */
+  int32_t tuned_segment[4]; /* the lengths timed ... */
+  float tuned_ms[4];        /* ... and their median trial times (ms) */
+} fdas_batch_info;
+int fdas_batch_get_info(const fdas_batch* batch, fdas_batch_info* info);
 
 /* Test hook: copies the float32 power plane of the last trial processed,
  * Z x nb row-major by z (P[j*nb + r] = |A(r, z_j)|^2, Eq. 1), to d_plane. */

@@ -488,6 +488,18 @@ int fdas_host_fresnel(double x, double* C, double* S) {
 struct fdas_batch {
   fdas_plan* base = nullptr;
   std::vector<fdas_plan*> views;
+  // captured CUDA graph of the last batch and the arguments it was made for
+  bool graphs = true;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const float*> key_series;
+  std::vector<int64_t> key_N;
+  fdas_cand* key_out = nullptr;
+  int64_t* key_counts = nullptr;
+  int64_t graph_builds = 0, graph_launches = 0;
+  // autotuner record
+  int n_tuned = 0;
+  int32_t tuned_segment[4] = {0, 0, 0, 0};
+  float tuned_ms[4] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -519,6 +531,46 @@ int batch_view(fdas_batch* b, int64_t N, fdas_plan** out) {
   return FDAS_OK;
 }
 
+// Median time of one trial (3 timed after 1 warm-up) of a fresh plan with
+// segment length L on the probe series.
+int time_segment(int64_t N, int32_t zmax, int32_t dz, int32_t m, int32_t L, int32_t nharm,
+                 float sigma, int64_t max_cands, const float* d_probe, cudaStream_t s,
+                 float* ms_out) {
+  fdas_plan* p = nullptr;
+  int rc = fdas_plan_create(&p, N, zmax, dz, m, L, nharm, sigma, max_cands, s);
+  if (rc) return rc;
+  cudaEvent_t ev[4];
+  int made = 0;
+  for (; made < 4 && !rc; ++made)
+    if (cudaEventCreate(&ev[made]) != cudaSuccess) rc = set_error(FDAS_ERR_CUDA, "cudaEventCreate failed");
+  float t[3] = {0, 0, 0};
+  if (!rc) rc = run_trial(p, d_probe, p->cands, p->count);
+  for (int i = 0; i < 3 && !rc; ++i) {
+    rc = cuda_check(cudaEventRecord(ev[0], s), "event");
+    if (!rc) rc = run_trial(p, d_probe, p->cands, p->count);
+    if (!rc) rc = cuda_check(cudaEventRecord(ev[1], s), "event");
+    if (!rc) rc = cuda_check(cudaEventSynchronize(ev[1]), "event sync");
+    if (!rc) rc = cuda_check(cudaEventElapsedTime(&t[i], ev[0], ev[1]), "elapsed");
+  }
+  for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+  fdas_plan_destroy(p);
+  if (rc) return rc;
+  std::sort(t, t + 3);
+  *ms_out = t[1];
+  return FDAS_OK;
+}
+
+// Trials of a batch in order, launched directly on the plan's stream.
+int batch_direct(const std::vector<fdas_plan*>& vs, const float* const* d_series,
+                 fdas_cand* d_out, int64_t* d_counts) {
+  for (size_t t = 0; t < vs.size(); ++t) {
+    int rc = run_trial(vs[t], d_series[t], d_out + t * vs[t]->max_cands,
+                       reinterpret_cast<unsigned long long*>(d_counts + t));
+    if (rc) return rc;
+  }
+  return FDAS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -536,9 +588,77 @@ int fdas_batch_create(fdas_batch** out, int64_t N_max, int32_t zmax, int32_t dz,
   return FDAS_OK;
 }
 
+int fdas_batch_create_tuned(fdas_batch** out, int64_t N_max, int32_t zmax, int32_t dz,
+                            int32_t m, int32_t nharm, float sigma, int64_t max_cands,
+                            const float* d_probe, void* stream) {
+  if (!out) return set_error(FDAS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int32_t cand[3] = {2048, 4096, 8192};
+  float* own = nullptr;
+  int rc = FDAS_OK;
+  if (!d_probe) {
+    if (N_max < (1 << 12) || N_max > (1 << 24))
+      return set_error(FDAS_ERR_INVALID, "N must be 2^a 3^b 5^c with a >= 12 and 2^12 <= N <= 2^24");
+    cudaError_t e = cudaMalloc((void**)&own, sizeof(float) * (size_t)N_max);
+    if (e != cudaSuccess) return set_error(FDAS_ERR_NOMEM, "probe series allocation failed");
+    rc = launch_probe_noise(own, N_max, 0x5eedull, s);
+    d_probe = own;
+  }
+  int n = 0, best = -1;
+  int32_t Ls[4] = {0, 0, 0, 0};
+  float ms[4] = {0, 0, 0, 0};
+  for (int i = 0; i < 3 && !rc; ++i) {
+    if (cand[i] < 2 * m) continue;
+    rc = time_segment(N_max, zmax, dz, m, cand[i], nharm, sigma, max_cands, d_probe, s, &ms[n]);
+    if (rc) break;
+    Ls[n] = cand[i];
+    if (best < 0 || ms[n] < ms[best]) best = n;
+    ++n;
+  }
+  if (own) {
+    cudaStreamSynchronize(s);
+    cudaFree(own);
+  }
+  if (rc) return rc;
+  if (best < 0) return set_error(FDAS_ERR_INVALID, "no segment length with L >= 2m");
+  rc = fdas_batch_create(out, N_max, zmax, dz, m, Ls[best], nharm, sigma, max_cands, stream);
+  if (rc) return rc;
+  (*out)->n_tuned = n;
+  for (int i = 0; i < n; ++i) {
+    (*out)->tuned_segment[i] = Ls[i];
+    (*out)->tuned_ms[i] = ms[i];
+  }
+  return FDAS_OK;
+}
+
+int fdas_batch_set_graphs(fdas_batch* b, int32_t enable) {
+  if (!b) return set_error(FDAS_ERR_INVALID, "NULL batch");
+  b->graphs = enable != 0;
+  return FDAS_OK;
+}
+
+int fdas_batch_get_info(const fdas_batch* b, fdas_batch_info* info) {
+  if (!b || !info) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  memset(info, 0, sizeof(*info));
+  info->N_max = b->base->N;
+  info->segment = b->base->L;
+  info->n_lengths = 1 + (int32_t)b->views.size();
+  info->graphs = b->graphs && b->base->stream != nullptr;
+  info->graph_builds = b->graph_builds;
+  info->graph_launches = b->graph_launches;
+  info->n_tuned = b->n_tuned;
+  for (int i = 0; i < 4; ++i) {
+    info->tuned_segment[i] = b->tuned_segment[i];
+    info->tuned_ms[i] = b->tuned_ms[i];
+  }
+  return FDAS_OK;
+}
+
 int fdas_batch_destroy(fdas_batch* b) {
   if (!b) return FDAS_OK;
   if (b->base && b->base->stream) cudaStreamSynchronize(b->base->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
   for (fdas_plan* v : b->views) {
     free_geometry_tables(v);
     delete v;
@@ -552,16 +672,56 @@ int fdas_search_batch(fdas_batch* b, const float* const* d_series, const int64_t
                       int32_t n_trials, fdas_cand* d_out, int64_t* d_counts) {
   if (!b || !d_series || !N || n_trials < 0 || (n_trials > 0 && (!d_out || !d_counts)))
     return set_error(FDAS_ERR_INVALID, "bad argument to fdas_search_batch");
+  // every length's geometry first: allocations cannot be captured
+  std::vector<fdas_plan*> vs((size_t)n_trials);
   for (int32_t t = 0; t < n_trials; ++t) {
     if (!d_series[t]) return set_error(FDAS_ERR_INVALID, "NULL series in batch");
-    fdas_plan* v = nullptr;
-    int rc = batch_view(b, N[t], &v);
-    if (rc) return rc;
-    rc = run_trial(v, d_series[t], d_out + (size_t)t * v->max_cands,
-                   reinterpret_cast<unsigned long long*>(d_counts + t));
+    int rc = batch_view(b, N[t], &vs[t]);
     if (rc) return rc;
   }
-  return FDAS_OK;
+  cudaStream_t s = b->base->stream;
+  // the legacy default stream cannot be captured
+  if (!b->graphs || s == nullptr || n_trials == 0) return batch_direct(vs, d_series, d_out, d_counts);
+  const bool same = b->exec && b->key_out == d_out && b->key_counts == d_counts &&
+                    b->key_series.size() == (size_t)n_trials &&
+                    std::equal(b->key_series.begin(), b->key_series.end(), d_series) &&
+                    std::equal(b->key_N.begin(), b->key_N.end(), N);
+  if (!same) {
+    int rc = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal),
+                        "begin capture");
+    if (rc) return rc;
+    const int trc = batch_direct(vs, d_series, d_out, d_counts);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (trc || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return trc ? trc : cuda_check(ce, "end capture");
+    }
+    if (b->exec) {
+      cudaGraphExecUpdateResultInfo upd;
+      if (cudaGraphExecUpdate(b->exec, g, &upd) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+      }
+    }
+    if (!b->exec) {
+      const cudaError_t ie = cudaGraphInstantiate(&b->exec, g, 0);
+      if (ie != cudaSuccess) {
+        b->exec = nullptr;
+        cudaGraphDestroy(g);
+        return cuda_check(ie, "graph instantiate");
+      }
+    }
+    cudaGraphDestroy(g);
+    ++b->graph_builds;
+    b->key_series.assign(d_series, d_series + n_trials);
+    b->key_N.assign(N, N + n_trials);
+    b->key_out = d_out;
+    b->key_counts = d_counts;
+  }
+  ++b->graph_launches;
+  return cuda_check(cudaGraphLaunch(b->exec, s), "graph launch");
 }
 
 const char* fdas_strerror(int status) {

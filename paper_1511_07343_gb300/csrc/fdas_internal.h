@@ -88,6 +88,9 @@ int gemm_check_shape(const fdas_plan* p);
 int launch_gemm_bank(fdas_plan* p);
 int launch_gemm_correlate(fdas_plan* p, float* d_plane);
 
+// fdas_tune.cu
+int launch_probe_noise(float* d_x, int64_t n, uint64_t seed, cudaStream_t s);
+
 // fdas_harmsum.cu
 int launch_pool4(fdas_plan* p, const float* d_plane, float* d_q4, fdas_cand* d_out,
                  unsigned long long* d_count);

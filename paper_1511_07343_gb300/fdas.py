@@ -41,6 +41,14 @@ class fdas_plan_info(ctypes.Structure):
                 ("corr_ctas_per_sm", ctypes.c_int32), ("corr_grid", ctypes.c_int32)]
 
 
+class fdas_batch_info(ctypes.Structure):
+    _fields_ = [("N_max", ctypes.c_int64), ("segment", ctypes.c_int32),
+                ("n_lengths", ctypes.c_int32), ("graphs", ctypes.c_int32),
+                ("n_tuned", ctypes.c_int32), ("graph_builds", ctypes.c_int64),
+                ("graph_launches", ctypes.c_int64), ("tuned_segment", ctypes.c_int32 * 4),
+                ("tuned_ms", ctypes.c_float * 4)]
+
+
 CAND_DTYPE = np.dtype([("r_top", "<i4"), ("z_idx", "<i4"), ("h", "<i4"), ("power", "<f4")])
 
 
@@ -77,6 +85,10 @@ _SIGS = {
     "fdas_profile_trial": [_P, _P, _P],
     "fdas_spectrum_noalloc": [_P, _I64, _P, _P],
     "fdas_plan_set_correlation": [_P, _I32],
+    "fdas_batch_create_tuned": [ctypes.POINTER(_P), _I64, _I32, _I32, _I32, _I32,
+                                ctypes.c_float, _I64, _P, _P],
+    "fdas_batch_set_graphs": [_P, _I32],
+    "fdas_batch_get_info": [_P, ctypes.POINTER(fdas_batch_info)],
     "fdas_host_fresnel": [ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_double)],
 }
@@ -170,6 +182,25 @@ def fdas_batch_create(N_max, zmax, dz, template_width, segment, nharm, sigma=6.0
                                     nharm, sigma, max_cands, _ptr(stream) or None),
            "fdas_batch_create")
     return batch.value
+
+
+def fdas_batch_create_tuned(N_max, zmax, dz, template_width, nharm, sigma=6.0,
+                            max_cands=1 << 20, d_probe=None, stream=0):
+    batch = _P()
+    _check(load().fdas_batch_create_tuned(ctypes.byref(batch), N_max, zmax, dz, template_width,
+                                          nharm, sigma, max_cands, _ptr(d_probe) or None,
+                                          _ptr(stream) or None), "fdas_batch_create_tuned")
+    return batch.value
+
+
+def fdas_batch_set_graphs(batch, enable):
+    _check(load().fdas_batch_set_graphs(batch, int(bool(enable))), "fdas_batch_set_graphs")
+
+
+def fdas_batch_get_info(batch) -> fdas_batch_info:
+    info = fdas_batch_info()
+    _check(load().fdas_batch_get_info(batch, ctypes.byref(info)), "fdas_batch_get_info")
+    return info
 
 
 def fdas_batch_destroy(batch):
