@@ -209,7 +209,7 @@ enum fdas_corr_mode {
  * feed the same harmonic sum and threshold. The left factor is built from the
  * plan's float64 taps when the mode is selected and held until the plan is
  * destroyed (2Z rounded up to 128 rows x 6m x 2 bytes).
- *   mode: an fdas_corr_mode. The GEMM modes need m % 32 == 0 and m <= 1024.
+ *   mode: an fdas_corr_mode. The GEMM modes need m % 32 == 0 and m <= 768.
  * A bounded device wait that gives up makes the next fdas_search return
  * FDAS_ERR_TIMEOUT. */
 int fdas_plan_set_correlation(fdas_plan* plan, int32_t mode);
