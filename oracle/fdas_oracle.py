@@ -18,7 +18,10 @@ Readings of the paper used here (the paper is silent or garbled on them):
     *mean* frequency is r (template centred on d = 0), Section 2; z = fdot T^2
     with T the observation length.
   * the spectrum keeps bins 0..N/2-1 (Nyquist dropped); whitening is a
-    64-bin running median (the step is not in the paper).
+    64-bin running median (the step is not in the paper). The block-median
+    variant takes medians of consecutive 64-bin blocks from bin 1, places
+    them at the block centres and interpolates linearly between centres
+    (constant beyond the first and last centre).
   * harmonic sums use round-half-up in r and round-half-away-from-zero in
     the centred z index; the threshold is the Gamma(h, 1) tail that equals
     the one-sided Gaussian tail at ``sigma``.
@@ -96,6 +99,33 @@ def whiten(X: np.ndarray, w: int = MEDIAN_WINDOW) -> np.ndarray:
     ln 2 times its mean, so whitened noise has unit mean power.
     """
     mu = running_median_power(X, w)
+    Xw = np.zeros_like(X, dtype=np.complex128)
+    Xw[1:] = X[1:] * np.sqrt(LN2 / mu[1:])
+    return Xw
+
+
+def block_median_power(X: np.ndarray, w: int = MEDIAN_WINDOW) -> np.ndarray:
+    """mu_k of the block-median variant: the textbook median of |X|^2 over
+    each block [1 + w b, min(1 + w (b+1), nb)) (the last block may be short),
+    placed at the block centre c_b = (first + last) / 2, then linear
+    interpolation in k between adjacent centres and the end medians beyond
+    the first and last centre; mu_0 is unused (nan)."""
+    nb = X.shape[0]
+    if nb < w + 1:
+        raise ValueError("spectrum too short for the median block")
+    p = np.abs(X) ** 2
+    starts = np.arange(1, nb, w)
+    ends = np.minimum(starts + w, nb)
+    med = np.array([np.median(p[a:b]) for a, b in zip(starts, ends)])
+    cen = 0.5 * (starts + ends - 1)
+    mu = np.interp(np.arange(nb, dtype=np.float64), cen, med)
+    mu[0] = np.nan
+    return mu
+
+
+def whiten_block(X: np.ndarray, w: int = MEDIAN_WINDOW) -> np.ndarray:
+    """Xw_k = X_k * sqrt(ln 2 / mu_k) with the block-median mu; Xw_0 = 0."""
+    mu = block_median_power(X, w)
     Xw = np.zeros_like(X, dtype=np.complex128)
     Xw[1:] = X[1:] * np.sqrt(LN2 / mu[1:])
     return Xw
@@ -284,10 +314,11 @@ def harmonic_sum_cells(Xw, taus, nharm: int, j_idx, r_idx) -> dict:
 # The whole path on one series.
 # ----------------------------------------------------------------------------
 def search(x: np.ndarray, zmax: int, dz: int, m: int, nharm: int,
-           sigma: float = 6.0):
-    """Returns (Xw, taus, P, candidate rows, harmonic sums)."""
+           sigma: float = 6.0, whitening: str = "running"):
+    """Returns (Xw, taus, P, candidate rows, harmonic sums); ``whitening`` is
+    "running" (64-bin running median) or "block" (block-median variant)."""
     X = spectrum(x)
-    Xw = whiten(X)
+    Xw = whiten(X) if whitening == "running" else whiten_block(X)
     taus = template_bank(zmax, dz, m)
     P = power_plane(Xw, taus)
     cands, H = candidates(P, nharm, sigma)

@@ -209,6 +209,70 @@ def test_whitening_constant_power_and_scale_invariance():
     assert np.allclose(O.whiten(7.5 * X), O.whiten(X), rtol=1e-12, atol=1e-14)
 
 
+# ------------------------------------------------- block-median whitening --
+def test_block_median_brute_force_small():
+    """Sorted-list medians of each block and the two-point interpolation
+    formula, written out with loops, on a spectrum whose last block is short."""
+    rng = np.random.default_rng(31)
+    nb = 64 * 5 + 18
+    X = rng.standard_normal(nb) + 1j * rng.standard_normal(nb)
+    p = [abs(v) ** 2 for v in X]
+    meds, cens = [], []
+    a = 1
+    while a < nb:
+        b = min(a + 64, nb)
+        vals = sorted(p[a:b])
+        c = len(vals)
+        meds.append(vals[c // 2] if c % 2 else 0.5 * (vals[c // 2 - 1] + vals[c // 2]))
+        cens.append((a + b - 1) / 2.0)
+        a = b
+    assert len(meds) == 6 and cens[-1] == (321 + 337) / 2.0
+    mu = O.block_median_power(X)
+    for k in range(1, nb):
+        if k <= cens[0]:
+            want = meds[0]
+        elif k >= cens[-1]:
+            want = meds[-1]
+        else:
+            i = max(i for i in range(len(cens)) if cens[i] <= k)
+            t = (k - cens[i]) / (cens[i + 1] - cens[i])
+            want = (1 - t) * meds[i] + t * meds[i + 1]
+        assert abs(mu[k] - want) <= 1e-12 * want, k
+    Xw = O.whiten_block(X)
+    assert Xw[0] == 0
+    assert np.allclose(np.abs(Xw[1:]) ** 2, np.array(p[1:]) * math.log(2) / mu[1:], rtol=1e-12)
+
+
+def test_block_median_linear_ramp_is_exact():
+    """A power ramp a + b k has each block median at its centre, so the
+    interpolation reproduces it exactly between the first and last centre and
+    the whitened power there is ln 2 (any plausible slip in the centres or the
+    interpolation breaks this)."""
+    nb = 64 * 9 + 40
+    k = np.arange(nb)
+    pw = 3.0 + 0.25 * k
+    X = np.sqrt(pw) * np.exp(1j * 0.37 * k)
+    mu = O.block_median_power(X)
+    inner = (k >= 32.5) & (k <= (1 + 64 * 9 + nb - 1) / 2.0)
+    assert np.allclose(mu[inner], pw[inner], rtol=1e-13)
+    assert np.allclose(mu[1:33], pw[32] + 0.125, rtol=1e-13)   # first centre 32.5
+    Xw = O.whiten_block(X)
+    assert np.allclose(np.abs(Xw[inner]) ** 2, math.log(2), rtol=1e-12)
+
+
+def test_block_median_constant_power_and_scale_invariance():
+    rng = np.random.default_rng(8)
+    nb = 4096 + 7
+    ph = np.exp(2j * np.pi * rng.random(nb))
+    Xw = O.whiten_block(2.5 * ph)
+    assert np.allclose(np.abs(Xw[1:]) ** 2, math.log(2), rtol=1e-12)
+    X = rng.standard_normal(nb) + 1j * rng.standard_normal(nb)
+    assert np.allclose(O.whiten_block(4.0 * X), O.whiten_block(X), rtol=1e-12, atol=1e-14)
+    # whitened noise has unit mean power
+    X = rng.standard_normal(1 << 18) + 1j * rng.standard_normal(1 << 18)
+    assert abs(np.mean(np.abs(O.whiten_block(X)[1:]) ** 2) - 1.0) < 0.02
+
+
 def test_whitening_rejects_short_spectrum():
     with pytest.raises(ValueError):
         O.whiten(np.ones(64, dtype=complex))
