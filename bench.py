@@ -597,6 +597,17 @@ def main():
                  "what": "unfused FP32 path: cuFFT (torch.fft) real FFT, segment and inverse FFTs, "
                          "elementwise multiply into a materialised complex plane, power, edge trim; "
                          "this library's whitening and harmonic sum"}
+    # the block-median whitening variant on the same plan and series
+    fdas.fdas_plan_set_whitening(plan, fdas.FDAS_WHITEN_BLOCK)
+    prof_b = np.stack([fdas.fdas_profile_trial(plan, d_series[i % len(d_series)])
+                       for i in range(3)])
+    fdas.fdas_plan_set_whitening(plan, fdas.FDAS_WHITEN_RUNNING)
+    whitening_variants = {
+        "running_median_ms": stage_ms["whiten"],
+        "block_median_ms": float(np.median(prof_b[:, 1])),
+        "block_trial_ms": float(np.median(prof_b.sum(axis=1))),
+        "what": "whitening stage time (CUDA events); block = medians of 64-bin blocks, "
+                "linearly interpolated"}
     variants_ref = None
     if rank == 0 and not args.no_variants and args.corr == "fft":
         ref_plane = torch.empty(info.Z * info.nb, dtype=torch.float32, device=dev)
@@ -653,6 +664,7 @@ def main():
                        "l2": f"{len(d_series)} resident series cycled; each step writes a "
                              f"{Z * nb * 4 / 1e9:.2f} GB plane (> L2)"},
             "stage_ms": stage_ms, "candidates_last_step": n_cands,
+            "whitening_variants": whitening_variants,
             "latency_ms": dict(percentiles(step_ms), what="per-trial device time, back to back"),
             "vs_plain_fp32": plain,
             "roofline": roof,

@@ -214,6 +214,20 @@ enum fdas_corr_mode {
  * FDAS_ERR_TIMEOUT. */
 int fdas_plan_set_correlation(fdas_plan* plan, int32_t mode);
 
+/* Whitening modes (the stage before step 3; not specified by the paper). */
+enum fdas_whiten_mode {
+  FDAS_WHITEN_RUNNING = 0, /* 64-bin running median, window [k-32, k+31] shifted into [1, nb-1] */
+  FDAS_WHITEN_BLOCK = 1    /* medians of 64-bin blocks from bin 1, linearly interpolated */
+};
+
+/* Selects the whitening of the plan. FDAS_WHITEN_BLOCK: mu_b = median of
+ * |X_k|^2 over [1 + 64 b, min(1 + 64 (b+1), nb)) (mean of the two middle
+ * values for an even count), placed at the block centre; mu_k interpolates
+ * linearly between adjacent centres and is constant beyond the first and
+ * last centre; Xw_k = X_k sqrt(ln 2 / mu_k), Xw_0 = 0. Cheaper than the
+ * running median but a different estimate, so candidate lists differ. */
+int fdas_plan_set_whitening(fdas_plan* plan, int32_t mode);
+
 /* Real FFT of one series without a plan and without allocating device memory.
  * The paper has no counterpart; this exists for callers that must not
  * allocate device memory (for example a real-time loop with a fixed device

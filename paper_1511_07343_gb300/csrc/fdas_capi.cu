@@ -394,6 +394,14 @@ int fdas_stage_plane(fdas_plan* p, const float* d_white, float* d_plane) {
   return launch_correlate(p, d_plane, nullptr, nullptr, nullptr);
 }
 
+int fdas_plan_set_whitening(fdas_plan* p, int32_t mode) {
+  if (!p) return set_error(FDAS_ERR_INVALID, "NULL plan");
+  if (mode != FDAS_WHITEN_RUNNING && mode != FDAS_WHITEN_BLOCK)
+    return set_error(FDAS_ERR_INVALID, "unknown whitening mode");
+  p->whiten_mode = mode;
+  return FDAS_OK;
+}
+
 int fdas_plan_set_correlation(fdas_plan* p, int32_t mode) {
   if (!p) return set_error(FDAS_ERR_INVALID, "NULL plan");
   if (mode != FDAS_CORR_FFT && mode != FDAS_CORR_GEMM_BF16 && mode != FDAS_CORR_GEMM_FP16)

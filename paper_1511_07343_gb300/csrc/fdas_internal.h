@@ -48,6 +48,7 @@ struct fdas_plan {
 
   // tensor-core correlation (precision variant); corr_mode = FDAS_CORR_*
   int corr_mode = 0;
+  int whiten_mode = 0;         // FDAS_WHITEN_*
   uint16_t* gbank = nullptr;   // 16-bit left factor, pre-tiled (see fdas_gemm.cu)
   int* gstatus = nullptr;      // device status word of the bounded waits
 
@@ -75,6 +76,7 @@ int launch_spectrum_mixed(fdas_plan* p, const float* d_series, float2* d_spec);
 bool is_235(int64_t x);
 bool split_235(int64_t M, int* M1, int* M2);
 int launch_whiten(fdas_plan* p, const float2* d_spec, float2* d_white);
+int launch_whiten_block(fdas_plan* p, const float2* d_spec, float2* d_white);
 
 // fdas_correlate.cu
 int launch_segments(fdas_plan* p, const float2* d_white);

@@ -225,6 +225,7 @@ int launch_spectrum(fdas_plan* p, const float* d_series, float2* d_spec) {
 }
 
 int launch_whiten(fdas_plan* p, const float2* d_spec, float2* d_white) {
+  if (p->whiten_mode == FDAS_WHITEN_BLOCK) return launch_whiten_block(p, d_spec, d_white);
   const unsigned nblk = (unsigned)((p->nb + kWTile - 1) / kWTile);
   k_whiten<<<nblk, kWTile, 0, p->stream>>>(d_spec, d_white, p->nb);
   return cuda_check(cudaGetLastError(), "k_whiten");

@@ -24,6 +24,8 @@ FDAS_ERR_OVERFLOW = -5
 FDAS_CORR_FFT = 0
 FDAS_CORR_GEMM_BF16 = 1
 FDAS_CORR_GEMM_FP16 = 2
+FDAS_WHITEN_RUNNING = 0
+FDAS_WHITEN_BLOCK = 1
 
 
 class fdas_cand(ctypes.Structure):
@@ -85,6 +87,7 @@ _SIGS = {
     "fdas_profile_trial": [_P, _P, _P],
     "fdas_spectrum_noalloc": [_P, _I64, _P, _P],
     "fdas_plan_set_correlation": [_P, _I32],
+    "fdas_plan_set_whitening": [_P, _I32],
     "fdas_batch_create_tuned": [ctypes.POINTER(_P), _I64, _I32, _I32, _I32, _I32,
                                 ctypes.c_float, _I64, _P, _P],
     "fdas_batch_set_graphs": [_P, _I32],
@@ -250,6 +253,10 @@ def fdas_profile_trial(plan, d_series):
     ms = np.zeros(5, dtype=np.float32)
     _check(load().fdas_profile_trial(plan, _ptr(d_series), ms.ctypes.data), "fdas_profile_trial")
     return ms
+
+
+def fdas_plan_set_whitening(plan, mode):
+    _check(load().fdas_plan_set_whitening(plan, mode), "fdas_plan_set_whitening")
 
 
 def fdas_plan_set_correlation(plan, mode):
