@@ -31,7 +31,7 @@ from __future__ import annotations
 import math
 
 import numpy as np
-from scipy import special
+from scipy import optimize, special
 
 LN2 = math.log(2.0)
 MEDIAN_WINDOW = 64
@@ -294,6 +294,65 @@ def candidates(P: np.ndarray, nharm: int, sigma: float = 6.0):
             rows.append((int(a), int(b), h, float(H[h][b, a])))
     rows.sort(key=lambda t: (t[2], t[0], t[1]))
     return rows, H
+
+
+# ----------------------------------------------------------------------------
+# Candidate distillation (after the threshold; not in the paper).
+# ----------------------------------------------------------------------------
+def log_gamma_tail(h: int, x: float) -> float:
+    """ln Q(h, x), the Gamma(h, 1) upper tail for integer h in its Poisson
+    form Q = exp(-x) sum_{k<h} x^k / k!, which does not underflow."""
+    s, term = 0.0, 1.0
+    for k in range(h):
+        if k > 0:
+            term *= x / k
+        s += term
+    return -x + math.log(s)
+
+
+def gaussian_sigma(log_p: float) -> float:
+    """The s with ln Phi_bar(s) = log_p (one-sided Gaussian tail): a bracketed
+    root of scipy's log_ndtr(-s) - log_p."""
+    def f(s):
+        return float(special.log_ndtr(-s)) - log_p
+    hi = 40.0
+    while f(hi) > 0:
+        hi *= 2.0
+    return float(optimize.brentq(f, -40.0, hi, xtol=1e-13, rtol=1e-15))
+
+
+def distill(rows, Z: int):
+    """Local maxima of a candidate list ``rows`` of (r, j, h, H):
+      * within level h, no candidate at (r + dr, j + dj), |dr|, |dj| <= 1,
+        has a larger H (equal H: the smaller (j, r) wins);
+      * across adjacent levels, candidates (r, jc) at level h and (r', jc') at
+        level 2h are the same signal when |r' - 2r| <= 2 and |jc' - 2 jc| <= 2
+        (jc = j - zc, zc = (Z-1)/2; a symmetric relation), and the one with
+        the larger sigma wins (equal sigma: the lower level).
+    Returns (r, j, h, H, sigma, log10 p) rows sorted by (h, r, j), with sigma
+    the Gaussian-equivalent significance of H under Gamma(h, 1) noise and
+    p = Q(h, H)."""
+    zc = (Z - 1) // 2
+    H = {(r, j, h): float(v) for (r, j, h, v) in rows}
+    lp = {key: log_gamma_tail(key[2], v) for key, v in H.items()}
+    sg = {key: gaussian_sigma(v) for key, v in lp.items()}
+    out = []
+    for (r, j, h), v in H.items():
+        me = (r, j, h)
+        keep = True
+        for (r2, j2, h2), w in H.items():
+            if h2 == h:
+                if max(abs(r2 - r), abs(j2 - j)) == 1 and (w > v or (w == v and (j2, r2) < (j, r))):
+                    keep = False
+            elif h2 == 2 * h or 2 * h2 == h:
+                lo, hi = ((r, j - zc), (r2, j2 - zc)) if h2 > h else ((r2, j2 - zc), (r, j - zc))
+                if abs(hi[0] - 2 * lo[0]) <= 2 and abs(hi[1] - 2 * lo[1]) <= 2:
+                    if sg[(r2, j2, h2)] > sg[me] or (sg[(r2, j2, h2)] == sg[me] and h2 < h):
+                        keep = False
+        if keep:
+            out.append((r, j, h, v, sg[me], lp[me] / math.log(10.0)))
+    out.sort(key=lambda t: (t[2], t[0], t[1]))
+    return out
 
 
 def harmonic_sum_cells(Xw, taus, nharm: int, j_idx, r_idx) -> dict:

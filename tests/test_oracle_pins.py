@@ -209,6 +209,79 @@ def test_whitening_constant_power_and_scale_invariance():
     assert np.allclose(O.whiten(7.5 * X), O.whiten(X), rtol=1e-12, atol=1e-14)
 
 
+# ------------------------------------------------------------ distillation --
+@pytest.mark.parametrize("h", [1, 2, 4, 8, 16])
+def test_log_gamma_tail_matches_library(h):
+    from scipy import special
+    for x in (0.5, 3.0, 17.0, 60.0, 200.0, 600.0):
+        want = math.log(special.gammaincc(h, x))
+        assert abs(O.log_gamma_tail(h, x) - want) <= 1e-11 * max(1.0, abs(want)), (h, x)
+
+
+def test_sigma_of_the_thresholds_is_six():
+    """T_h solves Q(h, T_h) = Phi_bar(6) (scipy's gammainccinv), so the
+    significance of a sum exactly at T_h is 6 at every level."""
+    T = O.thresholds(16, 6.0)
+    for h, t in T.items():
+        assert abs(O.gaussian_sigma(O.log_gamma_tail(h, t)) - 6.0) < 1e-8, h
+    assert abs(O.gaussian_sigma(math.log(O.gaussian_tail(3.25))) - 3.25) < 1e-10
+
+
+def test_sigma_far_tail_follows_the_asymptotic_series():
+    """For h = 1, ln p = -x; at large x the Gaussian tail obeys
+    ln Phi_bar(s) = -s^2/2 - ln(s sqrt(2 pi)) + ln(1 - 1/s^2 + 3/s^4 - 15/s^6 ...)."""
+    for x in (2.0e3, 5.0e4, 1.0e6):
+        s = O.gaussian_sigma(-x)
+        series = -s * s / 2 - math.log(s * math.sqrt(2 * math.pi)) + \
+            math.log(1 - 1 / s**2 + 3 / s**4 - 15 / s**6)
+        assert abs(series + x) < 1e-6 * x, x
+        assert s > math.sqrt(2 * x) * 0.95
+
+
+def test_distill_brute_force_cases():
+    Z = 21   # zc = 10
+    # a 3x3 blob at level 1: only its maximum survives; a cell two bins away too
+    blob = [(100 + dr, 10 + dj, 1, 25.0 + dr + 0.1 * dj) for dr in (-1, 0, 1) for dj in (-1, 0, 1)]
+    far = [(103, 10, 1, 22.0)]
+    out = O.distill(blob + far, Z)
+    assert [(r, j, h) for (r, j, h, *_) in out] == [(101, 11, 1), (103, 10, 1)]
+    # a plateau: equal H, the smaller (j, r) wins
+    out = O.distill([(50, 12, 2, 30.0), (51, 12, 2, 30.0), (50, 13, 2, 30.0)], Z)
+    assert [(r, j, h) for (r, j, h, *_) in out] == [(50, 12, 2)]
+    # across levels: the same signal at h = 1 (r, jc = 3) and h = 2 (2r + 1, 2 jc)
+    lo = (200, 13, 1, 40.0)          # sigma ~ 8.5
+    hi = (401, 16, 2, 60.0)
+    out = O.distill([lo, hi], Z)
+    assert [(r, j, h) for (r, j, h, *_) in out] == [(401, 16, 2)]
+    hi_weak = (400, 16, 2, 30.0)
+    out = O.distill([lo, hi_weak], Z)
+    assert [(r, j, h) for (r, j, h, *_) in out] == [(200, 13, 1)]
+    # the cross-level window is +-2 at the higher level, in the centred z
+    # index: jc' = -3 and jc = -2 (|-3 + 4| = 1) match, jc = -3 (distance 3)
+    # does not, nor does r' = 2r + 3
+    out = O.distill([(300, 7, 2, 80.0), (150, 8, 1, 30.0)], Z)
+    assert [(r, j, h) for (r, j, h, *_) in out] == [(300, 7, 2)]
+    out = O.distill([(300, 7, 2, 80.0), (150, 7, 1, 30.0)], Z)
+    assert [(r, j, h) for (r, j, h, *_) in out] == [(150, 7, 1), (300, 7, 2)]
+    out = O.distill([(303, 10, 2, 80.0), (150, 10, 1, 30.0)], Z)
+    assert len(out) == 2
+    out = O.distill([(302, 12, 2, 80.0), (151, 10, 1, 30.0), (150, 11, 1, 29.0)], Z)
+    assert [(r, j, h) for (r, j, h, *_) in out] == [(302, 12, 2)]
+    # the window is 8-connected: a diagonal neighbour alone suppresses
+    out = O.distill([(100, 10, 1, 25.0), (101, 11, 1, 30.0)], Z)
+    assert [(r, j, h) for (r, j, h, *_) in out] == [(101, 11, 1)]
+    # across levels sigma decides, not H: H = 26 at h = 2 is less
+    # significant than H = 25 at h = 1
+    assert O.gaussian_sigma(O.log_gamma_tail(2, 26.0)) < O.gaussian_sigma(-25.0)
+    out = O.distill([(200, 13, 1, 25.0), (400, 16, 2, 26.0)], Z)
+    assert [(r, j, h) for (r, j, h, *_) in out] == [(200, 13, 1)]
+    # sigma and log10 p of a survivor
+    (r, j, h, H, sig, l10) = O.distill([(10, 10, 4, 40.0)], Z)[0]
+    from scipy import special, stats
+    assert abs(l10 - math.log10(special.gammaincc(4, 40.0))) < 1e-10
+    assert abs(sig - stats.norm.isf(special.gammaincc(4, 40.0))) < 1e-8
+
+
 # ------------------------------------------------- block-median whitening --
 def test_block_median_brute_force_small():
     """Sorted-list medians of each block and the two-point interpolation
