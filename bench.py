@@ -597,6 +597,21 @@ def main():
                  "what": "unfused FP32 path: cuFFT (torch.fft) real FFT, segment and inverse FFTs, "
                          "elementwise multiply into a materialised complex plane, power, edge trim; "
                          "this library's whitening and harmonic sum"}
+    # candidate distillation of the last timed step's list
+    d_pk = torch.empty(max_cands * 24, dtype=torch.uint8, device=dev)
+    d_npk = torch.zeros(1, dtype=torch.int64, device=dev)
+    with torch.cuda.stream(stream):
+        fdas.fdas_distill(plan, d_out, d_cnt, d_pk, d_npk)   # first call builds the table
+        dev_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        dev_ev[0].record(stream)
+        for _ in range(5):
+            fdas.fdas_distill(plan, d_out, d_cnt, d_pk, d_npk)
+        dev_ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    distill = {"ms": dev_ev[0].elapsed_time(dev_ev[1]) / 5, "candidates": n_cands,
+               "peaks": int(d_npk.item()),
+               "what": "local maxima per level + cross-level matching, sigma per peak"}
+    del d_pk
     # the block-median whitening variant on the same plan and series
     fdas.fdas_plan_set_whitening(plan, fdas.FDAS_WHITEN_BLOCK)
     prof_b = np.stack([fdas.fdas_profile_trial(plan, d_series[i % len(d_series)])
@@ -665,6 +680,7 @@ def main():
                              f"{Z * nb * 4 / 1e9:.2f} GB plane (> L2)"},
             "stage_ms": stage_ms, "candidates_last_step": n_cands,
             "whitening_variants": whitening_variants,
+            "distill": distill,
             "latency_ms": dict(percentiles(step_ms), what="per-trial device time, back to back"),
             "vs_plain_fp32": plain,
             "roofline": roof,

@@ -214,6 +214,35 @@ enum fdas_corr_mode {
  * FDAS_ERR_TIMEOUT. */
 int fdas_plan_set_correlation(fdas_plan* plan, int32_t mode);
 
+/* One distilled detection: a local maximum of the candidate list with its
+ * Gaussian-equivalent significance. */
+typedef struct {
+  int32_t r_top;
+  int32_t z_idx;
+  int32_t h;
+  float power;    /* H_h */
+  float sigma;    /* Phi_bar(sigma) = Q(h, H_h), Q the Gamma(h, 1) upper tail */
+  float log10_p;  /* log10 Q(h, H_h), the per-cell false-alarm probability */
+} fdas_peak;
+
+/* Candidate distillation (after the threshold; not in the paper). From the
+ * first min(*d_count, max_cands) candidates at d_cands (device; the output
+ * of fdas_search_device or of one trial of fdas_search_batch), keeps those
+ * that are
+ *   - local maxima in H within their level: no candidate of the same h at
+ *     (r + dr, j + dj), |dr|, |dj| <= 1, has a larger H (equal H: the
+ *     smaller (j, r) wins), and
+ *   - the most significant rendering of their signal across adjacent levels:
+ *     candidates (r, jc) at level h and (r', jc') at level 2h, jc = j - zc,
+ *     zc = (Z-1)/2, count as one signal when |r' - 2r| <= 2 and
+ *     |jc' - 2 jc| <= 2; the larger sigma wins (equal: the lower level),
+ * writing them to d_peaks (device, max_cands entries, append order) and
+ * their exact number to *d_npeaks (device int64). Asynchronous on the plan's
+ * stream. The first call allocates a hash table of 2 x max_cands entries
+ * (12 bytes each), held by the plan. */
+int fdas_distill(fdas_plan* plan, const fdas_cand* d_cands, const int64_t* d_count,
+                 fdas_peak* d_peaks, int64_t* d_npeaks);
+
 /* Whitening modes (the stage before step 3; not specified by the paper). */
 enum fdas_whiten_mode {
   FDAS_WHITEN_RUNNING = 0, /* 64-bin running median, window [k-32, k+31] shifted into [1, nb-1] */

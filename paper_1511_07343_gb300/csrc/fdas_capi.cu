@@ -83,7 +83,8 @@ void free_plan(fdas_plan* p) {
   if (!p) return;
   void* ptrs[] = {p->tw_L, p->tw_M1, p->tw_M2, p->tw4_lo, p->tw4_hi, p->twN_lo, p->twN_hi,
                   p->taps, p->bank, p->series, p->zbuf, p->spec, p->spec2, p->white, p->seg,
-                  p->plane, p->q4, p->cands, p->count, p->gbank, p->gstatus};
+                  p->plane, p->q4, p->cands, p->count, p->gbank, p->gstatus,
+                  p->dkeys, p->dvals};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -392,6 +393,13 @@ int fdas_stage_plane(fdas_plan* p, const float* d_white, float* d_plane) {
   int rc = launch_segments(p, reinterpret_cast<const float2*>(d_white));
   if (rc) return rc;
   return launch_correlate(p, d_plane, nullptr, nullptr, nullptr);
+}
+
+int fdas_distill(fdas_plan* p, const fdas_cand* d_cands, const int64_t* d_count,
+                 fdas_peak* d_peaks, int64_t* d_npeaks) {
+  if (!p || !d_cands || !d_count || !d_peaks || !d_npeaks)
+    return set_error(FDAS_ERR_INVALID, "NULL argument");
+  return launch_distill(p, d_cands, d_count, d_peaks, d_npeaks);
 }
 
 int fdas_plan_set_whitening(fdas_plan* p, int32_t mode) {

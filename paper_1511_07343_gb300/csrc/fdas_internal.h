@@ -49,6 +49,10 @@ struct fdas_plan {
   // tensor-core correlation (precision variant); corr_mode = FDAS_CORR_*
   int corr_mode = 0;
   int whiten_mode = 0;         // FDAS_WHITEN_*
+  // candidate distillation: hash table of 2^dbits keys and values (on first use)
+  unsigned long long* dkeys = nullptr;
+  float* dvals = nullptr;
+  int dbits = 0;
   uint16_t* gbank = nullptr;   // 16-bit left factor, pre-tiled (see fdas_gemm.cu)
   int* gstatus = nullptr;      // device status word of the bounded waits
 
@@ -89,6 +93,10 @@ size_t gemm_bank_elems(const fdas_plan* p);
 int gemm_check_shape(const fdas_plan* p);
 int launch_gemm_bank(fdas_plan* p);
 int launch_gemm_correlate(fdas_plan* p, float* d_plane);
+
+// fdas_distill.cu
+int launch_distill(fdas_plan* p, const fdas_cand* d_cands, const int64_t* d_count,
+                   fdas_peak* d_peaks, int64_t* d_npeaks);
 
 // fdas_tune.cu
 int launch_probe_noise(float* d_x, int64_t n, uint64_t seed, cudaStream_t s);

@@ -52,6 +52,8 @@ class fdas_batch_info(ctypes.Structure):
 
 
 CAND_DTYPE = np.dtype([("r_top", "<i4"), ("z_idx", "<i4"), ("h", "<i4"), ("power", "<f4")])
+PEAK_DTYPE = np.dtype([("r_top", "<i4"), ("z_idx", "<i4"), ("h", "<i4"), ("power", "<f4"),
+                       ("sigma", "<f4"), ("log10_p", "<f4")])
 
 
 class FdasError(RuntimeError):
@@ -88,6 +90,7 @@ _SIGS = {
     "fdas_spectrum_noalloc": [_P, _I64, _P, _P],
     "fdas_plan_set_correlation": [_P, _I32],
     "fdas_plan_set_whitening": [_P, _I32],
+    "fdas_distill": [_P, _P, _P, _P, _P],
     "fdas_batch_create_tuned": [ctypes.POINTER(_P), _I64, _I32, _I32, _I32, _I32,
                                 ctypes.c_float, _I64, _P, _P],
     "fdas_batch_set_graphs": [_P, _I32],
@@ -253,6 +256,11 @@ def fdas_profile_trial(plan, d_series):
     ms = np.zeros(5, dtype=np.float32)
     _check(load().fdas_profile_trial(plan, _ptr(d_series), ms.ctypes.data), "fdas_profile_trial")
     return ms
+
+
+def fdas_distill(plan, d_cands, d_count, d_peaks, d_npeaks):
+    _check(load().fdas_distill(plan, _ptr(d_cands), _ptr(d_count), _ptr(d_peaks), _ptr(d_npeaks)),
+           "fdas_distill")
 
 
 def fdas_plan_set_whitening(plan, mode):
