@@ -185,9 +185,10 @@ def template_discrete(z: float, m: int, n: int) -> np.ndarray:
     return t[np.mod(d, n)]
 
 
-def template_bank(zmax: int, dz: int, m: int) -> np.ndarray:
-    """(Z, m) complex128 taps tau_{z_j}(d), rows j = 0..Z-1, z_j = -zmax + j dz."""
-    return np.stack([template_fresnel(z, m) for z in z_values(zmax, dz)])
+def template_bank(zmax: int, dz: int, m: int, offset: float = 0.0) -> np.ndarray:
+    """(Z, m) complex128 taps tau_{z_j}(d), rows j = 0..Z-1, z_j = -zmax + j dz
+    (at the fractional frequency offset ``offset``)."""
+    return np.stack([template_fresnel(z, m, offset) for z in z_values(zmax, dz)])
 
 
 # ----------------------------------------------------------------------------
@@ -215,6 +216,18 @@ def correlate_row(Xw: np.ndarray, tau: np.ndarray) -> np.ndarray:
 def power_plane(Xw: np.ndarray, taus: np.ndarray) -> np.ndarray:
     """P[j, r] = |A_j(r)|^2, shape (Z, nb), float64 (step 7: powers)."""
     return np.stack([np.abs(correlate_row(Xw, t)) ** 2 for t in taus])
+
+
+def power_plane_interbin(Xw: np.ndarray, zmax: int, dz: int, m: int) -> np.ndarray:
+    """The half-bin plane: P2[j, 2r + e] = |A(r + e/2, z_j)|^2, e = 0, 1, with
+    A(r + 1/2, z) = sum_d Xw[r+d] tau_z(d) at offset 1/2 (the same m taps
+    d = -m/2 .. m/2-1 around bin r); shape (Z, 2 nb), columns in half bins."""
+    P0 = power_plane(Xw, template_bank(zmax, dz, m))
+    P1 = power_plane(Xw, template_bank(zmax, dz, m, offset=0.5))
+    P2 = np.empty((P0.shape[0], 2 * P0.shape[1]))
+    P2[:, 0::2] = P0
+    P2[:, 1::2] = P1
+    return P2
 
 
 def plane_cells(Xw: np.ndarray, taus: np.ndarray, j_idx, r_idx) -> np.ndarray:
@@ -373,12 +386,14 @@ def harmonic_sum_cells(Xw, taus, nharm: int, j_idx, r_idx) -> dict:
 # The whole path on one series.
 # ----------------------------------------------------------------------------
 def search(x: np.ndarray, zmax: int, dz: int, m: int, nharm: int,
-           sigma: float = 6.0, whitening: str = "running"):
+           sigma: float = 6.0, whitening: str = "running", interbin: bool = False):
     """Returns (Xw, taus, P, candidate rows, harmonic sums); ``whitening`` is
-    "running" (64-bin running median) or "block" (block-median variant)."""
+    "running" (64-bin running median) or "block" (block-median variant);
+    with ``interbin`` the plane is the half-bin plane and every r (plane
+    column, candidate r_top) counts half bins."""
     X = spectrum(x)
     Xw = whiten(X) if whitening == "running" else whiten_block(X)
     taus = template_bank(zmax, dz, m)
-    P = power_plane(Xw, taus)
+    P = power_plane_interbin(Xw, zmax, dz, m) if interbin else power_plane(Xw, taus)
     cands, H = candidates(P, nharm, sigma)
     return Xw, taus, P, cands, H

@@ -209,6 +209,42 @@ def test_whitening_constant_power_and_scale_invariance():
     assert np.allclose(O.whiten(7.5 * X), O.whiten(X), rtol=1e-12, atol=1e-14)
 
 
+# ------------------------------------------------------- half-bin planes --
+@pytest.mark.parametrize("z", [0.0, 2.0, -2.0, 36.0, -50.0, 200.0])
+def test_half_bin_template_matches_the_defining_integral(z):
+    """tau_z(d) at offset 1/2 against adaptive quadrature of
+    int_0^1 exp(2 pi i [(d - 1/2 + z/2) u - z u^2/2]) du."""
+    from scipy import integrate
+    m = 64 if abs(z) < 100 else 512
+    tau = O.template_fresnel(z, m, offset=0.5)
+    for d in (-m // 2, -7, -1, 0, 1, 5, m // 2 - 1):
+        ph = lambda u: 2 * np.pi * ((d - 0.5 + z / 2) * u - z * u * u / 2)
+        lim = 400 if abs(z) < 100 else 4000
+        re = integrate.quad(lambda u: math.cos(ph(u)), 0, 1, limit=lim, epsabs=1e-13)[0]
+        im = integrate.quad(lambda u: math.sin(ph(u)), 0, 1, limit=lim, epsabs=1e-13)[0]
+        assert abs(tau[d + m // 2] - (re + 1j * im)) < 1e-10, (z, d)
+    if z == 0.0:   # the Fourier interpolation kernel i / (pi (d - 1/2))
+        d = np.arange(-m // 2, m // 2)
+        assert np.allclose(tau, 1j / (np.pi * (d - 0.5)), atol=1e-15)
+
+
+def test_half_bin_plane_recovers_a_half_bin_chirp():
+    """A noiseless chirp midway between bins: the half-bin plane column
+    2 r0 holds its full power s^2 (up to the m-tap truncation) at the true z,
+    while the integer columns lose about 60% to scalloping."""
+    n, s, r0, z0 = 1 << 14, 6.0, 2000.5, 20.0
+    x = make_series(n, 0, [Chirp(r0, z0, s, 0.4, 1)], noise=False)
+    Xw = O.spectrum(x) / math.sqrt(n)   # noiseless: unit-noise scaling, no whitening
+    P2 = O.power_plane_interbin(Xw, 30, 2, 128)
+    j0 = int((z0 + 30) // 2)
+    assert abs(P2[j0, 2 * 2000 + 1] / s**2 - 1.0) < 0.03
+    assert P2[j0, 4000] / s**2 < 0.5 and P2[j0, 4002] / s**2 < 0.5
+    assert np.unravel_index(np.argmax(P2), P2.shape) == (j0, 4001)
+    # the even columns are the integer plane
+    P = O.power_plane(Xw, O.template_bank(30, 2, 128))
+    assert np.array_equal(P2[:, 0::2], P)
+
+
 # ------------------------------------------------------------ distillation --
 @pytest.mark.parametrize("h", [1, 2, 4, 8, 16])
 def test_log_gamma_tail_matches_library(h):
