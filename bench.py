@@ -623,6 +623,19 @@ def main():
         "block_trial_ms": float(np.median(prof_b.sum(axis=1))),
         "what": "whitening stage time (CUDA events); block = medians of 64-bin blocks, "
                 "linearly interpolated"}
+    # half-bin planes (Z x 2 nb, the paper's Fig. 1 resolution) on the same plan
+    half_bin = None
+    if rank == 0 and not args.no_variants:
+        fdas.fdas_plan_set_interbin(plan, 1)
+        prof_h = np.stack([fdas.fdas_profile_trial(plan, d_series[i % len(d_series)])
+                           for i in range(3)])
+        fdas.fdas_plan_set_interbin(plan, 0)
+        half_bin = {
+            "trial_ms": float(np.median(prof_h.sum(axis=1))),
+            "value": 1e3 / float(np.median(prof_h.sum(axis=1))), "unit": "trials/s",
+            "stage_ms": {s: float(np.median(prof_h[:, i])) for i, s in enumerate(stages)},
+            "what": "2Z template rows (offsets 0 and 1/2), plane of Z x 2nb half bins; "
+                    "harmsum stage includes the 4-bin maxima kernel"}
     variants_ref = None
     if rank == 0 and not args.no_variants and args.corr == "fft":
         ref_plane = torch.empty(info.Z * info.nb, dtype=torch.float32, device=dev)
@@ -681,6 +694,7 @@ def main():
             "stage_ms": stage_ms, "candidates_last_step": n_cands,
             "whitening_variants": whitening_variants,
             "distill": distill,
+            "half_bin_plane": half_bin,
             "latency_ms": dict(percentiles(step_ms), what="per-trial device time, back to back"),
             "vs_plain_fp32": plain,
             "roofline": roof,

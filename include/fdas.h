@@ -243,6 +243,20 @@ typedef struct {
 int fdas_distill(fdas_plan* plan, const fdas_cand* d_cands, const int64_t* d_count,
                  fdas_peak* d_peaks, int64_t* d_npeaks);
 
+/* Half-bin (interbinned) planes, the resolution of the paper's Fig. 1:
+ * with enable != 0 the plan also evaluates Eq. 1 at the half-integer
+ * frequencies r + 1/2, with templates tau_z at frequency offset 1/2 (the same
+ * m taps d = -m/2..m/2-1 around bin r; Fresnel form with q = d - 1/2 + z/2),
+ * and the plane becomes P[j][2r + e] = |A(r + e/2, z_j)|^2, e = 0, 1: Z rows
+ * of 2 nb columns counted in half bins. Harmonic sums and thresholds run
+ * unchanged on that plane, so candidate r_top is in half bins (frequency
+ * r_top / 2 bins). The first call builds the 2Z-row template bank and
+ * doubles the plane and 4-bin-maxima buffers (synchronises the stream);
+ * fdas_plane_debug then copies Z x 2nb floats, and fdas_stage_plane writes
+ * that many. FFT correlation only (FDAS_ERR_INVALID in a tensor-core mode).
+ * enable = 0 returns to the integer plane. */
+int fdas_plan_set_interbin(fdas_plan* plan, int32_t enable);
+
 /* Whitening modes (the stage before step 3; not specified by the paper). */
 enum fdas_whiten_mode {
   FDAS_WHITEN_RUNNING = 0, /* 64-bin running median, window [k-32, k+31] shifted into [1, nb-1] */

@@ -84,7 +84,7 @@ void free_plan(fdas_plan* p) {
   void* ptrs[] = {p->tw_L, p->tw_M1, p->tw_M2, p->tw4_lo, p->tw4_hi, p->twN_lo, p->twN_hi,
                   p->taps, p->bank, p->series, p->zbuf, p->spec, p->spec2, p->white, p->seg,
                   p->plane, p->q4, p->cands, p->count, p->gbank, p->gstatus,
-                  p->dkeys, p->dvals};
+                  p->dkeys, p->dvals, p->taps_ib, p->bank_ib};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -112,7 +112,9 @@ int launch_plane(fdas_plan* p, float* d_plane, float* d_q4, fdas_cand* d_out,
   int rc;
   if (p->corr_mode == FDAS_CORR_FFT) {
     if ((rc = launch_segments(p, p->white))) return rc;
-    return launch_correlate(p, d_plane, d_q4, d_out, d_count);
+    if ((rc = launch_correlate(p, d_plane, d_q4, d_out, d_count))) return rc;
+    // half-bin planes: maxima and h = 1 candidates of the interleaved plane
+    return p->interbin && d_q4 ? launch_pool4(p, d_plane, d_q4, d_out, d_count) : FDAS_OK;
   }
   if ((rc = launch_gemm_correlate(p, d_plane))) return rc;
   return d_q4 ? launch_pool4(p, d_plane, d_q4, d_out, d_count) : FDAS_OK;
@@ -283,6 +285,7 @@ int fdas_plan_create(fdas_plan** out, int64_t N, int32_t zmax, int32_t dz, int32
   TRY(dalloc(p, &p->seg, (size_t)p->S * L));
   TRY(dalloc(p, &p->plane, (size_t)p->Z * p->nb));
   TRY(dalloc(p, &p->q4, (size_t)p->Z * (p->nb / 4)));
+  p->plane_cap = (int64_t)p->Z * p->nb;
   TRY(dalloc(p, &p->cands, (size_t)max_cands));
   TRY(dalloc(p, &p->count, 1));
 
@@ -320,7 +323,7 @@ int fdas_plan_get_info(const fdas_plan* p, fdas_plan_info* info) {
   for (int i = 0; i < 5; ++i) info->thresholds[i] = p->thr[i];
   info->max_cands = p->max_cands;
   info->device_bytes = p->device_bytes;
-  info->plane_floats = (int64_t)p->Z * p->nb;
+  info->plane_floats = (int64_t)p->Z * plane_width(p);
   info->corr_ctas_per_sm = p->corr_ctas_per_sm;
   info->corr_grid = p->corr_grid;
   return FDAS_OK;
@@ -364,7 +367,7 @@ int fdas_search_device(fdas_plan* p, const float* d_series, int32_t n_trials, fd
 
 int fdas_plane_debug(fdas_plan* p, float* d_plane) {
   if (!p || !d_plane) return set_error(FDAS_ERR_INVALID, "NULL argument");
-  return cuda_check(cudaMemcpyAsync(d_plane, p->plane, sizeof(float) * (size_t)p->Z * p->nb,
+  return cuda_check(cudaMemcpyAsync(d_plane, p->plane, sizeof(float) * (size_t)p->Z * plane_width(p),
                                     cudaMemcpyDeviceToDevice, p->stream),
                     "copy plane");
 }
@@ -402,6 +405,37 @@ int fdas_distill(fdas_plan* p, const fdas_cand* d_cands, const int64_t* d_count,
   return launch_distill(p, d_cands, d_count, d_peaks, d_npeaks);
 }
 
+int fdas_plan_set_interbin(fdas_plan* p, int32_t enable) {
+  if (!p) return set_error(FDAS_ERR_INVALID, "NULL plan");
+  if (!enable) {
+    p->interbin = 0;
+    return FDAS_OK;
+  }
+  if (p->corr_mode != FDAS_CORR_FFT)
+    return set_error(FDAS_ERR_INVALID, "half-bin planes use the FFT correlation only");
+  int rc;
+  if (!p->taps_ib) {
+    if ((rc = dalloc(p, &p->taps_ib, (size_t)2 * p->Z * p->m))) return rc;
+    if ((rc = dalloc(p, &p->bank_ib, (size_t)2 * p->Z * p->L))) return rc;
+    if ((rc = launch_template_interbin(p))) return rc;
+  }
+  const int64_t need = (int64_t)p->Z * 2 * p->nb;
+  if (p->plane_cap < need) {
+    if ((rc = cuda_check(cudaStreamSynchronize(p->stream), "sync"))) return rc;
+    cudaFree(p->plane);
+    cudaFree(p->q4);
+    p->device_bytes -= (int64_t)sizeof(float) * (p->plane_cap + p->plane_cap / 4);
+    p->plane = nullptr;
+    p->q4 = nullptr;
+    p->plane_cap = 0;
+    if ((rc = dalloc(p, &p->plane, (size_t)need))) return rc;
+    if ((rc = dalloc(p, &p->q4, (size_t)need / 4))) return rc;
+    p->plane_cap = need;
+  }
+  p->interbin = 1;
+  return cuda_check(cudaStreamSynchronize(p->stream), "half-bin templates");
+}
+
 int fdas_plan_set_whitening(fdas_plan* p, int32_t mode) {
   if (!p) return set_error(FDAS_ERR_INVALID, "NULL plan");
   if (mode != FDAS_WHITEN_RUNNING && mode != FDAS_WHITEN_BLOCK)
@@ -418,6 +452,8 @@ int fdas_plan_set_correlation(fdas_plan* p, int32_t mode) {
     p->corr_mode = mode;
     return FDAS_OK;
   }
+  if (p->interbin)
+    return set_error(FDAS_ERR_INVALID, "half-bin planes use the FFT correlation only");
   int rc = gemm_check_shape(p);
   if (rc) return rc;
   if (!p->gbank && (rc = dalloc(p, &p->gbank, gemm_bank_elems(p)))) return rc;
@@ -472,11 +508,12 @@ int fdas_profile_trial(fdas_plan* p, const float* d_series, float* h_ms) {
   if (!rc) rc = cuda_check(cudaEventRecord(ev[2], p->stream), "event");
   // the tensor-core modes have no segment FFTs; their 4-bin maxima and h = 1
   // threshold (a separate kernel there) count as harmonic-sum time
-  const bool fft = p->corr_mode == FDAS_CORR_FFT;
-  if (!rc && fft) rc = launch_segments(p, p->white);
+  const bool fft = p->corr_mode == FDAS_CORR_FFT && !p->interbin;
+  if (!rc && p->corr_mode == FDAS_CORR_FFT) rc = launch_segments(p, p->white);
   if (!rc) rc = cuda_check(cudaEventRecord(ev[3], p->stream), "event");
   if (!rc) rc = fft ? launch_correlate(p, p->plane, p->q4, p->cands, p->count)
-                    : launch_gemm_correlate(p, p->plane);
+                    : p->interbin ? launch_correlate(p, p->plane, nullptr, nullptr, nullptr)
+                                  : launch_gemm_correlate(p, p->plane);
   if (!rc) rc = cuda_check(cudaEventRecord(ev[4], p->stream), "event");
   if (!rc && !fft) rc = launch_pool4(p, p->plane, p->q4, p->cands, p->count);
   if (!rc) rc = launch_harmsum(p, p->plane, p->q4, p->cands, p->count);

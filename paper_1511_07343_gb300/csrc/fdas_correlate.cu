@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
     k_correlate_fused(const float4* __restrict__ seg4, const float4* __restrict__ bank4,
                       float* __restrict__ plane, float* __restrict__ q4, int64_t nb, int Z, int V,
                       int m, int64_t n_pairs, const float2* __restrict__ twL, float thr1,
-                      fdas_cand* __restrict__ cands, unsigned long long* count, int64_t maxc) {
+                      fdas_cand* __restrict__ cands, unsigned long long* count, int64_t maxc,
+                      int ib) {
   using C = Corr<L>;
   constexpr int T = C::T, NA = C::NA, RA2 = C::RA2, NB2 = C::NB2, X2P = C::X2P;
   constexpr int L2 = L / 2;
@@ -235,14 +236,26 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
     int64_t nvalid = nb - r0;
     if (nvalid > V) nvalid = V;
     const int n4 = (int)(nvalid >> 2);
-    float* prow = plane ? plane + (size_t)z * nb + r0 : nullptr;
+    // (half-bin planes, ib = 1: template row z = 2j + e fills columns 2r + e
+    // of plane row j; rows 2j and 2j+1 are consecutive pairs, so each sector
+    // is completed in L2 before it is written back)
+    float* prow = plane ? plane + (size_t)(z >> ib) * (nb << ib) + (r0 << ib) + (z & ib) : nullptr;
     float* qrow = q4 ? q4 + (size_t)z * nq + (r0 >> 2) : nullptr;
     const float4* P4 = reinterpret_cast<const float4*>(Ps);
     bool hit = false;
     for (int k = tid; k < n4; k += T) {
       const float4 p4 = P4[k];
       const float mx = fmaxf(fmaxf(p4.x, p4.y), fmaxf(p4.z, p4.w));
-      if (prow) reinterpret_cast<float4*>(prow)[k] = p4;
+      if (prow) {
+        if (ib) {
+          prow[8 * k] = p4.x;
+          prow[8 * k + 2] = p4.y;
+          prow[8 * k + 4] = p4.z;
+          prow[8 * k + 6] = p4.w;
+        } else {
+          reinterpret_cast<float4*>(prow)[k] = p4;
+        }
+      }
       if (qrow) qrow[k] = mx;
       hit |= mx >= thr1;
     }
@@ -326,13 +339,19 @@ int corr_launch(fdas_plan* p, float* plane, float* q4, fdas_cand* cands,
   if (occ > C::MAXCTA) occ = C::MAXCTA;
   if (occ < 1) return set_error(FDAS_ERR_CUDA, "k_correlate_fused cannot be resident");
   p->corr_ctas_per_sm = occ;
-  const int64_t n_pairs = (int64_t)p->S * p->Z;
+  // half-bin planes: 2Z template rows, the plane alone (4-bin maxima and
+  // h = 1 candidates of the interleaved plane come from k_pool4)
+  const int ib = p->interbin;
+  const int zrows = p->Z << ib;
+  const int64_t n_pairs = (int64_t)p->S * zrows;
   int64_t grid = (int64_t)occ * sms;
   if (grid > n_pairs) grid = n_pairs;
   p->corr_grid = (int)grid;
   k_correlate_fused<L><<<(unsigned)grid, C::T, smem, p->stream>>>(
-      reinterpret_cast<const float4*>(p->seg), reinterpret_cast<const float4*>(p->bank), plane,
-      q4, p->nb, p->Z, p->V, p->m, n_pairs, p->tw_L, p->thr[0], cands, count, p->max_cands);
+      reinterpret_cast<const float4*>(p->seg),
+      reinterpret_cast<const float4*>(ib ? p->bank_ib : p->bank), plane, ib ? nullptr : q4, p->nb,
+      zrows, p->V, p->m, n_pairs, p->tw_L, p->thr[0], ib ? nullptr : cands, count, p->max_cands,
+      ib);
   return cuda_check(cudaGetLastError(), "k_correlate_fused");
 }
 

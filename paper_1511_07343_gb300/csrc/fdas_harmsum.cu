@@ -261,9 +261,10 @@ Thr thresholds_of(const fdas_plan* p) {
 
 int launch_pool4(fdas_plan* p, const float* d_plane, float* d_q4, fdas_cand* d_out,
                  unsigned long long* d_count) {
-  const int64_t nq = p->nb >> 2;
+  const int64_t w = plane_width(p);
+  const int64_t nq = w >> 2;
   dim3 grid((unsigned)((nq + 255) / 256), p->Z);
-  k_pool4<<<grid, 256, 0, p->stream>>>(d_plane, d_q4, p->nb, p->thr[0], d_out, d_count,
+  k_pool4<<<grid, 256, 0, p->stream>>>(d_plane, d_q4, w, p->thr[0], d_out, d_count,
                                        p->max_cands);
   return cuda_check(cudaGetLastError(), "k_pool4");
 }
@@ -271,7 +272,8 @@ int launch_pool4(fdas_plan* p, const float* d_plane, float* d_q4, fdas_cand* d_o
 int launch_harmsum(fdas_plan* p, const float* d_plane, const float* d_q4, fdas_cand* d_out,
                    unsigned long long* d_count) {
   if (p->n_levels < 2) return FDAS_OK;
-  dim3 grid((unsigned)((p->nb + kHsSpan - 1) / kHsSpan), p->Z);
+  const int64_t w = plane_width(p);
+  dim3 grid((unsigned)((w + kHsSpan - 1) / kHsSpan), p->Z);
   const Thr thr = thresholds_of(p);
   static bool attr_set[6] = {false, false, false, false, false, false};
   if (!attr_set[p->n_levels]) {
@@ -287,19 +289,19 @@ int launch_harmsum(fdas_plan* p, const float* d_plane, const float* d_q4, fdas_c
   }
   switch (p->n_levels) {
     case 2:
-      k_harmsum_staged<2><<<grid, kHsThreads, kHsSmem, p->stream>>>(d_plane, d_q4, p->nb, p->Z, thr,
+      k_harmsum_staged<2><<<grid, kHsThreads, kHsSmem, p->stream>>>(d_plane, d_q4, w, p->Z, thr,
                                                             d_out, d_count, p->max_cands);
       break;
     case 3:
-      k_harmsum_staged<3><<<grid, kHsThreads, kHsSmem, p->stream>>>(d_plane, d_q4, p->nb, p->Z, thr,
+      k_harmsum_staged<3><<<grid, kHsThreads, kHsSmem, p->stream>>>(d_plane, d_q4, w, p->Z, thr,
                                                             d_out, d_count, p->max_cands);
       break;
     case 4:
-      k_harmsum_staged<4><<<grid, kHsThreads, kHsSmem, p->stream>>>(d_plane, d_q4, p->nb, p->Z, thr,
+      k_harmsum_staged<4><<<grid, kHsThreads, kHsSmem, p->stream>>>(d_plane, d_q4, w, p->Z, thr,
                                                             d_out, d_count, p->max_cands);
       break;
     default:
-      k_harmsum_staged<5><<<grid, kHsThreads, kHsSmem, p->stream>>>(d_plane, d_q4, p->nb, p->Z, thr,
+      k_harmsum_staged<5><<<grid, kHsThreads, kHsSmem, p->stream>>>(d_plane, d_q4, w, p->Z, thr,
                                                             d_out, d_count, p->max_cands);
   }
   return cuda_check(cudaGetLastError(), "k_harmsum_staged");

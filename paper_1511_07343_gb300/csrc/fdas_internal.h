@@ -49,6 +49,12 @@ struct fdas_plan {
   // tensor-core correlation (precision variant); corr_mode = FDAS_CORR_*
   int corr_mode = 0;
   int whiten_mode = 0;         // FDAS_WHITEN_*
+  // half-bin planes: taps and spectra of 2Z template rows (row 2j + e at
+  // frequency offset e/2); the plane and Q4 then have 2 nb columns
+  int interbin = 0;
+  double2* taps_ib = nullptr;
+  float2* bank_ib = nullptr;
+  int64_t plane_cap = 0;       // floats the plane buffer holds (Q4: plane_cap / 4)
   // candidate distillation: hash table of 2^dbits keys and values (on first use)
   unsigned long long* dkeys = nullptr;
   float* dvals = nullptr;
@@ -63,6 +69,9 @@ struct fdas_plan {
 
 namespace fdas {
 
+// plane columns: nb, or 2 nb (half bins) for half-bin planes
+inline int64_t plane_width(const fdas_plan* p) { return p->nb << p->interbin; }
+
 // error plumbing
 int set_error(int code, const std::string& msg);
 int cuda_check(cudaError_t e, const char* what);
@@ -71,6 +80,7 @@ int cuda_check(cudaError_t e, const char* what);
 int launch_twiddles(float2* out, int64_t count, int64_t mult, int64_t period, cudaStream_t s);
 int launch_template_taps(fdas_plan* p);
 int launch_template_bank(fdas_plan* p);
+int launch_template_interbin(fdas_plan* p);
 void fresnel_host(double x, double* C, double* S);
 
 // fdas_spectrum.cu, fdas_spectrum_mixed.cu

@@ -127,12 +127,17 @@ HD cd fresnel_diff(double s0, double c0, double sn0, double s1, double c1, doubl
   return F(s1, c1, sn1, t1) - F(s0, c0, sn0, t0);
 }
 
-// tau_z(d) for integer z = zi and d = di (float64).
-HD cd template_tap(int zi, int di) {
-  if (zi == 0) return di == 0 ? mk(1.0, 0.0) : mk(0.0, 0.0);
+// tau_z at q = d - offset + z/2 for integer z = zi, given Q = 2q (an
+// integer for integer d and z and offsets 0 or 1/2), float64.
+HD cd template_tap_q2(int zi, long long Q) {
+  if (zi == 0) {
+    // int_0^1 exp(2 pi i q u) du: delta at q = 0 for integer q; for
+    // half-integer q, exp(2 pi i q) = -1 gives i / (pi q)
+    if ((Q & 1) == 0) return Q == 0 ? mk(1.0, 0.0) : mk(0.0, 0.0);
+    return mk(0.0, 2.0 / (3.14159265358979323846 * (double)Q));
+  }
   const int az = zi < 0 ? -zi : zi;
   const double sg = zi < 0 ? -1.0 : 1.0;
-  const long long Q = 2LL * di + zi;  // Q = 2q
   const double q = 0.5 * (double)Q;
   const double scale = sqrt(2.0 * az);
   const double s0 = scale * (0.0 - q / zi);
@@ -153,13 +158,20 @@ HD cd template_tap(int zi, int di) {
   return mk(t.re / scale, -t.im / scale);
 }
 
-__global__ void k_template_taps(double2* __restrict__ taps, int Z, int m, int zmax, int dz) {
+// tau_z(d) for integer z = zi and d = di (float64).
+HD cd template_tap(int zi, int di) { return template_tap_q2(zi, 2LL * di + zi); }
+
+// rows = 1: row j holds tau_{z_j}; rows = 2: row 2j + e holds tau_{z_j} at
+// frequency offset e/2 (the half-bin bank), q = d - e/2 + z/2.
+__global__ void k_template_taps(double2* __restrict__ taps, int Z, int m, int zmax, int dz,
+                                int rows) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
-  if (i >= m || j >= Z) return;
+  const int row = blockIdx.y;
+  if (i >= m || row >= Z * rows) return;
+  const int j = row / rows, e = row % rows;
   const int z = -zmax + j * dz;
-  const cd t = template_tap(z, i - m / 2);
-  taps[(size_t)j * m + i] = make_double2(t.re, t.im);
+  const cd t = template_tap_q2(z, 2LL * (i - m / 2) + z - e);
+  taps[(size_t)row * m + i] = make_double2(t.re, t.im);
 }
 
 // bank[j][k] = (1/L) sum_i taps[j][i] exp(+2 pi i k (i - m/2) / L), float64
@@ -220,7 +232,7 @@ int launch_twiddles(float2* out, int64_t count, int64_t mult, int64_t period, cu
 
 int launch_template_taps(fdas_plan* p) {
   dim3 grid((p->m + 127) / 128, p->Z);
-  k_template_taps<<<grid, 128, 0, p->stream>>>(p->taps, p->Z, p->m, p->zmax, p->dz);
+  k_template_taps<<<grid, 128, 0, p->stream>>>(p->taps, p->Z, p->m, p->zmax, p->dz, 1);
   return cuda_check(cudaGetLastError(), "k_template_taps");
 }
 
@@ -229,6 +241,17 @@ int launch_template_bank(fdas_plan* p) {
   const size_t smem = sizeof(double2) * p->m;
   k_template_bank<<<grid, 128, smem, p->stream>>>(p->taps, p->bank, p->m, p->L);
   return cuda_check(cudaGetLastError(), "k_template_bank");
+}
+
+int launch_template_interbin(fdas_plan* p) {
+  dim3 tgrid((p->m + 127) / 128, 2 * p->Z);
+  k_template_taps<<<tgrid, 128, 0, p->stream>>>(p->taps_ib, p->Z, p->m, p->zmax, p->dz, 2);
+  int rc = cuda_check(cudaGetLastError(), "k_template_taps (half-bin)");
+  if (rc) return rc;
+  dim3 grid((p->L + 127) / 128, 2 * p->Z);
+  const size_t smem = sizeof(double2) * p->m;
+  k_template_bank<<<grid, 128, smem, p->stream>>>(p->taps_ib, p->bank_ib, p->m, p->L);
+  return cuda_check(cudaGetLastError(), "k_template_bank (half-bin)");
 }
 
 void fresnel_host(double x, double* C, double* S) {

@@ -90,6 +90,7 @@ _SIGS = {
     "fdas_spectrum_noalloc": [_P, _I64, _P, _P],
     "fdas_plan_set_correlation": [_P, _I32],
     "fdas_plan_set_whitening": [_P, _I32],
+    "fdas_plan_set_interbin": [_P, _I32],
     "fdas_distill": [_P, _P, _P, _P, _P],
     "fdas_batch_create_tuned": [ctypes.POINTER(_P), _I64, _I32, _I32, _I32, _I32,
                                 ctypes.c_float, _I64, _P, _P],
@@ -261,6 +262,10 @@ def fdas_profile_trial(plan, d_series):
 def fdas_distill(plan, d_cands, d_count, d_peaks, d_npeaks):
     _check(load().fdas_distill(plan, _ptr(d_cands), _ptr(d_count), _ptr(d_peaks), _ptr(d_npeaks)),
            "fdas_distill")
+
+
+def fdas_plan_set_interbin(plan, enable):
+    _check(load().fdas_plan_set_interbin(plan, int(bool(enable))), "fdas_plan_set_interbin")
 
 
 def fdas_plan_set_whitening(plan, mode):
