@@ -87,13 +87,13 @@ struct Corr {
 FDAS_DEV c2 c2_of(float4 v) { return c2{make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
 FDAS_DEV float4 f4_of(c2 v) { return make_float4(v.re.x, v.re.y, v.im.x, v.im.y); }
 
-template <int L>
+template <int L, int IB>
 __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
     k_correlate_fused(const float4* __restrict__ seg4, const float4* __restrict__ bank4,
                       float* __restrict__ plane, float* __restrict__ q4, int64_t nb, int Z, int V,
                       int m, int64_t n_pairs, const float2* __restrict__ twL, float thr1,
-                      fdas_cand* __restrict__ cands, unsigned long long* count, int64_t maxc,
-                      int ib) {
+                      fdas_cand* __restrict__ cands, unsigned long long* count, int64_t maxc) {
+  constexpr int ib = IB;
   using C = Corr<L>;
   constexpr int T = C::T, NA = C::NA, RA2 = C::RA2, NB2 = C::NB2, X2P = C::X2P;
   constexpr int L2 = L / 2;
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
       const float4 p4 = P4[k];
       const float mx = fmaxf(fmaxf(p4.x, p4.y), fmaxf(p4.z, p4.w));
       if (prow) {
-        if (ib) {
+        if constexpr (IB) {
           prow[8 * k] = p4.x;
           prow[8 * k + 2] = p4.y;
           prow[8 * k + 4] = p4.z;
@@ -303,7 +303,7 @@ int seg_launch(fdas_plan* p, const float2* Xw) {
   return cuda_check(cudaGetLastError(), "k_segments");
 }
 
-template <int L>
+template <int L, int IB>
 int corr_launch(fdas_plan* p, float* plane, float* q4, fdas_cand* cands,
                 unsigned long long* count) {
   using C = Corr<L>;
@@ -316,17 +316,17 @@ int corr_launch(fdas_plan* p, float* plane, float* q4, fdas_cand* cands,
   size_t smem = C::SMEM;
   const size_t cap = (size_t)smem_sm / (C::MAXCTA + 1) + 1;
   if (smem + 1024 < cap) smem = cap - 1024 + 16;
-  cudaError_t e = cudaFuncSetAttribute(k_correlate_fused<L>,
+  cudaError_t e = cudaFuncSetAttribute(k_correlate_fused<L, IB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_check(e, "k_correlate_fused attr");
-  e = cudaFuncSetAttribute(k_correlate_fused<L>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  e = cudaFuncSetAttribute(k_correlate_fused<L, IB>, cudaFuncAttributePreferredSharedMemoryCarveout,
                            (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return cuda_check(e, "k_correlate_fused carveout");
   // Resident CTAs per SM from the kernel's own resource use (registers in
   // units of 8 per thread, shared memory incl. the 1 KB per-CTA reserve,
   // threads), capped by the tensor-memory budget.
   cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, k_correlate_fused<L>);
+  e = cudaFuncGetAttributes(&fa, k_correlate_fused<L, IB>);
   if (e != cudaSuccess) return cuda_check(e, "k_correlate_fused attributes");
   int regs_sm = 0, thr_sm = 0;
   cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
@@ -341,17 +341,16 @@ int corr_launch(fdas_plan* p, float* plane, float* q4, fdas_cand* cands,
   p->corr_ctas_per_sm = occ;
   // half-bin planes: 2Z template rows, the plane alone (4-bin maxima and
   // h = 1 candidates of the interleaved plane come from k_pool4)
-  const int ib = p->interbin;
+  constexpr int ib = IB;
   const int zrows = p->Z << ib;
   const int64_t n_pairs = (int64_t)p->S * zrows;
   int64_t grid = (int64_t)occ * sms;
   if (grid > n_pairs) grid = n_pairs;
   p->corr_grid = (int)grid;
-  k_correlate_fused<L><<<(unsigned)grid, C::T, smem, p->stream>>>(
+  k_correlate_fused<L, IB><<<(unsigned)grid, C::T, smem, p->stream>>>(
       reinterpret_cast<const float4*>(p->seg),
       reinterpret_cast<const float4*>(ib ? p->bank_ib : p->bank), plane, ib ? nullptr : q4, p->nb,
-      zrows, p->V, p->m, n_pairs, p->tw_L, p->thr[0], ib ? nullptr : cands, count, p->max_cands,
-      ib);
+      zrows, p->V, p->m, n_pairs, p->tw_L, p->thr[0], ib ? nullptr : cands, count, p->max_cands);
   return cuda_check(cudaGetLastError(), "k_correlate_fused");
 }
 
@@ -386,9 +385,15 @@ int launch_segments(fdas_plan* p, const float2* d_white) {
 int launch_correlate(fdas_plan* p, float* d_plane, float* d_q4, fdas_cand* d_cands,
                      unsigned long long* d_count) {
   switch (p->L) {
-    case 2048: return corr_launch<2048>(p, d_plane, d_q4, d_cands, d_count);
-    case 4096: return corr_launch<4096>(p, d_plane, d_q4, d_cands, d_count);
-    case 8192: return corr_launch<8192>(p, d_plane, d_q4, d_cands, d_count);
+    case 2048:
+      return p->interbin ? corr_launch<2048, 1>(p, d_plane, d_q4, d_cands, d_count)
+                         : corr_launch<2048, 0>(p, d_plane, d_q4, d_cands, d_count);
+    case 4096:
+      return p->interbin ? corr_launch<4096, 1>(p, d_plane, d_q4, d_cands, d_count)
+                         : corr_launch<4096, 0>(p, d_plane, d_q4, d_cands, d_count);
+    case 8192:
+      return p->interbin ? corr_launch<8192, 1>(p, d_plane, d_q4, d_cands, d_count)
+                         : corr_launch<8192, 0>(p, d_plane, d_q4, d_cands, d_count);
   }
   return set_error(FDAS_ERR_INVALID, "unsupported segment length");
 }
