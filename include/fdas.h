@@ -98,8 +98,13 @@ int fdas_search(fdas_plan* plan, const float* d_series, int32_t n_trials,
                 fdas_cand* h_out, int64_t* h_counts);
 
 /* As fdas_search, but the series are in host memory (step 1 of Section 4:
- * the transfer to the GPU is part of the call; page-locked memory makes it
- * asynchronous). */
+ * the transfer to the GPU is part of the call). With n_trials > 1 on a
+ * stream other than the legacy default stream, the copies overlap the
+ * kernels: series t+1 is copied in (on a copy stream of the plan, into a
+ * second staging buffer) and trial t-1's candidates are read back and
+ * sorted while trial t runs; page-locked host memory is needed for the
+ * copies to overlap. The first such call allocates the second staging
+ * buffer and candidate list (4N + 16 max_cands bytes). */
 int fdas_search_host(fdas_plan* plan, const float* h_series, int32_t n_trials,
                      fdas_cand* h_out, int64_t* h_counts);
 

@@ -81,6 +81,14 @@ int dalloc(fdas_plan* p, T** ptr, size_t count) {
 
 void free_plan(fdas_plan* p) {
   if (!p) return;
+  for (int b = 0; b < 2; ++b) {
+    if (p->ev_in[b]) cudaEventDestroy(p->ev_in[b]);
+    if (p->ev_done[b]) cudaEventDestroy(p->ev_done[b]);
+  }
+  if (p->cstream) cudaStreamDestroy(p->cstream);
+  if (p->series2) cudaFree(p->series2);
+  if (p->cands2) cudaFree(p->cands2);
+  if (p->count2) cudaFree(p->count2);
   void* ptrs[] = {p->tw_L, p->tw_M1, p->tw_M2, p->tw4_lo, p->tw4_hi, p->twN_lo, p->twN_hi,
                   p->taps, p->bank, p->series, p->zbuf, p->spec, p->spec2, p->white, p->seg,
                   p->plane, p->q4, p->cands, p->count, p->gbank, p->gstatus,
@@ -219,6 +227,88 @@ int search_impl(fdas_plan* p, const float* d_series, int32_t n_trials, fdas_cand
   return overflow ? set_error(FDAS_ERR_OVERFLOW, "candidate list overflow") : FDAS_OK;
 }
 
+// Several host series through one plan with the copies overlapped: while
+// trial t runs on the plan stream, the copy stream brings in series t+1
+// (into the other staging buffer, once trial t-1 has finished reading it)
+// and the host reads back and sorts the candidates of trial t-1 (from the
+// other candidate buffer). Page-locked host memory makes the copies overlap.
+int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_cand* h_out,
+                  int64_t* h_counts) {
+  int rc;
+  if (!p->series2) {
+    if ((rc = dalloc(p, &p->series2, (size_t)p->N))) return rc;
+    if ((rc = dalloc(p, &p->cands2, (size_t)p->max_cands))) return rc;
+    if ((rc = dalloc(p, &p->count2, 1))) return rc;
+    if ((rc = cuda_check(cudaStreamCreateWithFlags(&p->cstream, cudaStreamNonBlocking),
+                         "copy stream")))
+      return rc;
+    for (int b = 0; b < 2 && !rc; ++b) {
+      rc = cuda_check(cudaEventCreateWithFlags(&p->ev_in[b], cudaEventDisableTiming), "event");
+      if (!rc)
+        rc = cuda_check(cudaEventCreateWithFlags(&p->ev_done[b], cudaEventDisableTiming), "event");
+    }
+    if (rc) return rc;
+  }
+  float* buf[2] = {p->series, p->series2};
+  fdas_cand* cbuf[2] = {p->cands, p->cands2};
+  unsigned long long* nbuf[2] = {p->count, p->count2};
+  const size_t bytes = sizeof(float) * (size_t)p->N;
+  bool overflow = false;
+  // read back and sort trial t (its kernels are done once ev_done fires)
+  auto finish = [&](int32_t t) -> int {
+    const int b = t & 1;
+    int r = cuda_check(cudaEventSynchronize(p->ev_done[b]), "trial done");
+    unsigned long long cnt = 0;
+    if (!r)
+      r = cuda_check(cudaMemcpyAsync(&cnt, nbuf[b], sizeof(cnt), cudaMemcpyDeviceToHost, p->cstream),
+                     "copy count");
+    if (!r) r = cuda_check(cudaStreamSynchronize(p->cstream), "sync count");
+    if (r) return r;
+    h_counts[t] = (int64_t)cnt;
+    const int64_t keep = std::min<int64_t>((int64_t)cnt, p->max_cands);
+    if ((int64_t)cnt > p->max_cands) overflow = true;
+    fdas_cand* dst = h_out + (size_t)t * p->max_cands;
+    if (keep > 0) {
+      r = cuda_check(cudaMemcpyAsync(dst, cbuf[b], sizeof(fdas_cand) * keep,
+                                     cudaMemcpyDeviceToHost, p->cstream),
+                     "copy candidates");
+      if (!r) r = cuda_check(cudaStreamSynchronize(p->cstream), "sync candidates");
+      if (r) return r;
+      std::sort(dst, dst + keep, cand_less);
+    }
+    return FDAS_OK;
+  };
+  rc = cuda_check(cudaMemcpyAsync(buf[0], h_series, bytes, cudaMemcpyHostToDevice, p->cstream),
+                  "copy series");
+  if (!rc) rc = cuda_check(cudaEventRecord(p->ev_in[0], p->cstream), "event");
+  for (int32_t t = 0; t < n_trials && !rc; ++t) {
+    const int b = t & 1, o = b ^ 1;
+    if (t + 1 < n_trials) {
+      // staging buffer o was last read by trial t-1
+      if (t >= 1) rc = cuda_check(cudaStreamWaitEvent(p->cstream, p->ev_done[o], 0), "wait");
+      if (!rc)
+        rc = cuda_check(cudaMemcpyAsync(buf[o], h_series + (size_t)(t + 1) * p->N, bytes,
+                                        cudaMemcpyHostToDevice, p->cstream),
+                        "copy series");
+      if (!rc) rc = cuda_check(cudaEventRecord(p->ev_in[o], p->cstream), "event");
+    }
+    if (!rc) rc = cuda_check(cudaStreamWaitEvent(p->stream, p->ev_in[b], 0), "wait");
+    if (!rc) rc = run_trial(p, buf[b], cbuf[b], nbuf[b]);
+    if (!rc) rc = cuda_check(cudaEventRecord(p->ev_done[b], p->stream), "event");
+    // the host reads back trial t-1 while trial t runs; trial t+1 reuses
+    // its candidate buffer only after this returns
+    if (!rc && t >= 1) rc = finish(t - 1);
+  }
+  if (!rc && n_trials >= 1) rc = finish(n_trials - 1);
+  if (!rc) rc = gemm_status(p);
+  if (rc) {
+    cudaStreamSynchronize(p->cstream);
+    cudaStreamSynchronize(p->stream);
+    return rc;
+  }
+  return overflow ? set_error(FDAS_ERR_OVERFLOW, "candidate list overflow") : FDAS_OK;
+}
+
 }  // namespace
 }  // namespace fdas
 
@@ -340,17 +430,23 @@ int fdas_search_host(fdas_plan* p, const float* h_series, int32_t n_trials, fdas
                      int64_t* h_counts) {
   if (!p || !h_series || n_trials < 0 || (n_trials > 0 && (!h_out || !h_counts)))
     return set_error(FDAS_ERR_INVALID, "bad argument to fdas_search_host");
-  bool overflow = false;
-  for (int32_t t = 0; t < n_trials; ++t) {
-    int rc = cuda_check(cudaMemcpyAsync(p->series, h_series + (size_t)t * p->N,
-                                        sizeof(float) * p->N, cudaMemcpyHostToDevice, p->stream),
-                        "copy series");
-    if (rc) return rc;
-    rc = search_impl(p, p->series, 1, h_out + (size_t)t * p->max_cands, h_counts + t);
-    if (rc == FDAS_ERR_OVERFLOW) overflow = true;
-    else if (rc) return rc;
+  if (n_trials == 1 || p->stream == nullptr) {
+    // one trial (or the legacy default stream, which orders every copy after
+    // every kernel): copy, run, read back in sequence
+    bool overflow = false;
+    for (int32_t t = 0; t < n_trials; ++t) {
+      int rc = cuda_check(cudaMemcpyAsync(p->series, h_series + (size_t)t * p->N,
+                                          sizeof(float) * p->N, cudaMemcpyHostToDevice,
+                                          p->stream),
+                          "copy series");
+      if (rc) return rc;
+      rc = search_impl(p, p->series, 1, h_out + (size_t)t * p->max_cands, h_counts + t);
+      if (rc == FDAS_ERR_OVERFLOW) overflow = true;
+      else if (rc) return rc;
+    }
+    return overflow ? set_error(FDAS_ERR_OVERFLOW, "candidate list overflow") : FDAS_OK;
   }
-  return overflow ? set_error(FDAS_ERR_OVERFLOW, "candidate list overflow") : FDAS_OK;
+  return host_pipeline(p, h_series, n_trials, h_out, h_counts);
 }
 
 int fdas_search_device(fdas_plan* p, const float* d_series, int32_t n_trials, fdas_cand* d_out,

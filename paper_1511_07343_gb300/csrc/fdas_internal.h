@@ -62,6 +62,15 @@ struct fdas_plan {
   uint16_t* gbank = nullptr;   // 16-bit left factor, pre-tiled (see fdas_gemm.cu)
   int* gstatus = nullptr;      // device status word of the bounded waits
 
+  // host-input pipeline (second staging buffer, candidate list and count,
+  // a copy stream and events; made on the first multi-trial host call)
+  float* series2 = nullptr;
+  fdas_cand* cands2 = nullptr;
+  unsigned long long* count2 = nullptr;
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr};    // series copy landed
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};  // trial finished on the plan stream
+
   int64_t device_bytes = 0;
   int corr_ctas_per_sm = 0;  // launch shape of the correlation kernel (last launch)
   int corr_grid = 0;

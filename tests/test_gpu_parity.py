@@ -335,3 +335,35 @@ def test_full_size_2e23_zmax200_sampled(gpu_lib):
     for j, r in zip(js[top], rs[top]):
         if r >= 1:
             assert (int(r), int(j), 1) in gk
+
+
+def test_host_pipeline_equals_single_trials(gpu_lib):
+    """Several host series in one fdas_search_host call on a non-default
+    stream (copies overlapped with the previous trial's kernels): every
+    trial's sorted list and count equal those of one-trial calls, for
+    page-locked and for pageable host memory."""
+    fd = gpu_lib
+    N = 1 << 15
+    xs = np.stack([make_series(N, 900 + t, [Chirp(1500.0 + 700 * t, 4.0 * t - 8, 8.0, 0.2, 4)])
+                   for t in range(5)])
+    stream = torch.cuda.Stream(DEV)
+    plan = fd.fdas_plan_create(N, 30, 2, 128, 2048, 8, 6.0, 2048, stream.cuda_stream)
+    try:
+        info = fd.fdas_plan_get_info(plan)
+        single = []
+        for t in range(5):
+            o = np.zeros(info.max_cands, dtype=fd.CAND_DTYPE)
+            c = np.zeros(1, dtype=np.int64)
+            fd.fdas_search_host(plan, np.ascontiguousarray(xs[t]), 1, o, c)
+            single.append((int(c[0]), o[:c[0]].tobytes()))
+        pinned = torch.from_numpy(xs.ravel().copy()).pin_memory()
+        for src in (pinned.numpy(), np.ascontiguousarray(xs.ravel())):
+            out = np.zeros(5 * info.max_cands, dtype=fd.CAND_DTYPE)
+            cnt = np.zeros(5, dtype=np.int64)
+            fd.fdas_search_host(plan, src, 5, out, cnt)
+            for t in range(5):
+                got = out[t * info.max_cands: t * info.max_cands + cnt[t]]
+                assert (int(cnt[t]), got.tobytes()) == single[t], t
+    finally:
+        fd.fdas_plan_destroy(plan)
+    assert all(c > 0 for c, _ in single)
