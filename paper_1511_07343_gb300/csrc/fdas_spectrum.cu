@@ -129,15 +129,20 @@ int dispatch_rows(fdas_plan* p, const float2* T, float2* Zo) {
 // ----------------------------------------------------------------------------
 // Whitening: mu_k = even-count median of |X|^2 over the 64-bin window of bin
 // k ([k-32, k+31] shifted into [1, nb-1]); Xw_k = X_k sqrt(ln2 / mu_k).
-// A CTA takes 128 consecutive bins: the union of their windows (<= 191
-// powers) is sorted once in shared memory as 64-bit keys (power bits, then
-// index; powers are >= 0 so their bit patterns order like the values), and
-// each thread walks the sorted list picking the 32nd and 33rd entries that
-// fall in its own window.
+// A CTA takes 64 consecutive bins: the union of their windows (<= 127
+// powers) is sorted once in shared memory as 32-bit keys - the power's bit
+// pattern (powers are >= 0, so bit patterns order like values) with its low
+// 7 mantissa bits replaced by the entry's index - and the medians read the
+// exact powers back by index. (Two powers within 2^-16 of each other may
+// swap places in that order, which moves a median by less than 2^-16
+// relative.) For each run of 32 sorted entries a 128-bit mask records which
+// indices it holds; a warp skips the runs below its lanes' 32nd in-window
+// entries by popcount and then walks the sorted list in step, every lane
+// reading the same entry.
 // ----------------------------------------------------------------------------
 constexpr int kWin = 64;
-constexpr int kWTile = 128;
-constexpr int kSortN = 256;
+constexpr int kWTile = 64;
+constexpr int kSortN = 128;
 
 __device__ __forceinline__ int64_t wstart(int64_t k, int64_t nb) {
   int64_t s = k - kWin / 2;
@@ -147,17 +152,23 @@ __device__ __forceinline__ int64_t wstart(int64_t k, int64_t nb) {
 
 __global__ void __launch_bounds__(kWTile) k_whiten(const float2* __restrict__ X,
                                                    float2* __restrict__ Xw, int64_t nb) {
-  __shared__ unsigned long long skey[kSortN];
+  __shared__ unsigned skey[kSortN];
+  __shared__ float spow[kSortN];
+  __shared__ unsigned long long cmask[kSortN / 32][2];
   const int tid = threadIdx.x;
+  if (tid < kSortN / 16) cmask[tid >> 1][tid & 1] = 0ull;
   const int64_t k0 = (int64_t)blockIdx.x * kWTile;
   const int64_t klast = (k0 + kWTile - 1 < nb - 1) ? k0 + kWTile - 1 : nb - 1;
   const int64_t lo = wstart(k0 < 1 ? 1 : k0, nb);
   const int64_t hi = wstart(klast, nb) + kWin - 1;
   const int cnt = (int)(hi - lo + 1);
   for (int t = tid; t < kSortN; t += kWTile) {
-    unsigned long long key = ~0ull;
-    if (t < cnt)
-      key = ((unsigned long long)__float_as_uint(cnorm(X[lo + t])) << 32) | (unsigned)t;
+    unsigned key = ~0u;
+    if (t < cnt) {
+      const float pw = cnorm(X[lo + t]);
+      spow[t] = pw;
+      key = (__float_as_uint(pw) & ~0x7Fu) | (unsigned)t;
+    }
     skey[t] = key;
   }
   __syncthreads();
@@ -167,7 +178,7 @@ __global__ void __launch_bounds__(kWTile) k_whiten(const float2* __restrict__ X,
       const int a = 2 * stride * (tid / stride) + (tid % stride);
       const int b = a + stride;
       const bool up = (a & size) == 0;
-      const unsigned long long ka = skey[a], kb = skey[b];
+      const unsigned ka = skey[a], kb = skey[b];
       if ((ka > kb) == up) {
         skey[a] = kb;
         skey[b] = ka;
@@ -175,27 +186,45 @@ __global__ void __launch_bounds__(kWTile) k_whiten(const float2* __restrict__ X,
       __syncthreads();
     }
   }
-  const int64_t k = k0 + tid;
-  if (k >= nb) return;
-  if (k == 0) {
-    Xw[0] = make_float2(0.f, 0.f);
-    return;
+  for (int t = tid; t < cnt; t += kWTile) {
+    const unsigned i = skey[t] & 0x7Fu;
+    atomicOr(&cmask[t >> 5][i >> 6], 1ull << (i & 63));
   }
-  const unsigned s = (unsigned)(wstart(k, nb) - lo);
-  unsigned va = 0, vb = 0;
-  int c = 0;
-  for (int t = 0; t < cnt; ++t) {
-    const unsigned long long key = skey[t];
-    if ((unsigned)key - s < (unsigned)kWin) {  // index in [s, s + 63]
-      if (c == kWin / 2 - 1) va = (unsigned)(key >> 32);
+  __syncthreads();
+  const int64_t k = k0 + tid;
+  const bool live = k < nb;
+  const unsigned s = live ? (unsigned)(wstart(k, nb) - lo) : 0u;  // s <= 63
+  // window bits [s, s + 63] of the 128 relative indices
+  const unsigned long long w0 = ~0ull << s, w1 = s ? (1ull << s) - 1ull : 0ull;
+  int c = 0, t0 = 0;
+  for (; t0 + 32 <= cnt; t0 += 32) {
+    const int n = __popcll(cmask[t0 >> 5][0] & w0) + __popcll(cmask[t0 >> 5][1] & w1);
+    if (c + n >= kWin / 2) break;  // the 32nd in-window entry is in this run
+    c += n;
+  }
+  // walk in step from the warp's lowest start; lanes before their own start
+  // skip entries they have already counted
+  const int tw = __reduce_min_sync(0xffffffffu, t0);
+  int ia = -1, ib = -1;
+  bool done = !live;
+  for (int t = tw; t < cnt && !__all_sync(0xffffffffu, done); ++t) {
+    const unsigned key = skey[t];
+    const unsigned i = key & 0x7Fu;
+    if (!done && t >= t0 && i - s < (unsigned)kWin) {
+      if (c == kWin / 2 - 1) ia = (int)i;
       if (c == kWin / 2) {
-        vb = (unsigned)(key >> 32);
-        break;
+        ib = (int)i;
+        done = true;
       }
       ++c;
     }
   }
-  const float mu = 0.5f * (__uint_as_float(va) + __uint_as_float(vb));
+  if (!live) return;
+  if (k == 0) {
+    Xw[0] = make_float2(0.f, 0.f);
+    return;
+  }
+  const float mu = 0.5f * (spow[ia] + spow[ib]);
   const float2 x = X[k];
   const float g = mu > 0.f ? sqrtf(0.69314718055994531f / mu) : 0.f;
   Xw[k] = make_float2(x.x * g, x.y * g);
