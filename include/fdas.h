@@ -93,7 +93,10 @@ int fdas_plan_get_info(const fdas_plan* plan, fdas_plan_info* info);
  * Candidates of trial t go to h_out + t*max_cands (host, caller-owned),
  * sorted by (h, r_top, z_idx); h_counts[t] is the exact number found, which
  * may exceed max_cands: then only max_cands are stored and the call returns
- * FDAS_ERR_OVERFLOW after finishing every trial. Synchronises the stream. */
+ * FDAS_ERR_OVERFLOW after finishing every trial. Synchronises the stream.
+ * With n_trials > 1 on a stream other than the legacy default stream, trial
+ * t-1's candidates are read back and sorted while trial t runs (a second
+ * candidate list, allocated on first use, alternates with the first). */
 int fdas_search(fdas_plan* plan, const float* d_series, int32_t n_trials,
                 fdas_cand* h_out, int64_t* h_counts);
 

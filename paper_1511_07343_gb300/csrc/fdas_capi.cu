@@ -232,8 +232,10 @@ int search_impl(fdas_plan* p, const float* d_series, int32_t n_trials, fdas_cand
 // (into the other staging buffer, once trial t-1 has finished reading it)
 // and the host reads back and sorts the candidates of trial t-1 (from the
 // other candidate buffer). Page-locked host memory makes the copies overlap.
+// (d_series != nullptr: the series are already on the device, nothing is
+// copied in and only the read-back overlaps)
 int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_cand* h_out,
-                  int64_t* h_counts) {
+                  int64_t* h_counts, const float* d_series = nullptr) {
   int rc;
   if (!p->series2) {
     if ((rc = dalloc(p, &p->series2, (size_t)p->N))) return rc;
@@ -278,11 +280,19 @@ int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_ca
     }
     return FDAS_OK;
   };
-  rc = cuda_check(cudaMemcpyAsync(buf[0], h_series, bytes, cudaMemcpyHostToDevice, p->cstream),
-                  "copy series");
-  if (!rc) rc = cuda_check(cudaEventRecord(p->ev_in[0], p->cstream), "event");
+  if (!d_series) {
+    rc = cuda_check(cudaMemcpyAsync(buf[0], h_series, bytes, cudaMemcpyHostToDevice, p->cstream),
+                    "copy series");
+    if (!rc) rc = cuda_check(cudaEventRecord(p->ev_in[0], p->cstream), "event");
+  }
   for (int32_t t = 0; t < n_trials && !rc; ++t) {
     const int b = t & 1, o = b ^ 1;
+    if (d_series) {
+      rc = run_trial(p, d_series + (size_t)t * p->N, cbuf[b], nbuf[b]);
+      if (!rc) rc = cuda_check(cudaEventRecord(p->ev_done[b], p->stream), "event");
+      if (!rc && t >= 1) rc = finish(t - 1);
+      continue;
+    }
     if (t + 1 < n_trials) {
       // staging buffer o was last read by trial t-1
       if (t >= 1) rc = cuda_check(cudaStreamWaitEvent(p->cstream, p->ev_done[o], 0), "wait");
@@ -423,6 +433,8 @@ int fdas_search(fdas_plan* p, const float* d_series, int32_t n_trials, fdas_cand
                 int64_t* h_counts) {
   if (!p || !d_series || n_trials < 0 || (n_trials > 0 && (!h_out || !h_counts)))
     return set_error(FDAS_ERR_INVALID, "bad argument to fdas_search");
+  if (n_trials > 1 && p->stream != nullptr)  // read-back of trial t-1 overlaps trial t
+    return host_pipeline(p, nullptr, n_trials, h_out, h_counts, d_series);
   return search_impl(p, d_series, n_trials, h_out, h_counts);
 }
 

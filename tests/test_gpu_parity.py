@@ -338,10 +338,11 @@ def test_full_size_2e23_zmax200_sampled(gpu_lib):
 
 
 def test_host_pipeline_equals_single_trials(gpu_lib):
-    """Several host series in one fdas_search_host call on a non-default
-    stream (copies overlapped with the previous trial's kernels): every
+    """Several series in one call on a non-default stream (copies and
+    read-back overlapped with the neighbouring trials' kernels): every
     trial's sorted list and count equal those of one-trial calls, for
-    page-locked and for pageable host memory."""
+    page-locked and pageable host series (fdas_search_host) and for device
+    series (fdas_search)."""
     fd = gpu_lib
     N = 1 << 15
     xs = np.stack([make_series(N, 900 + t, [Chirp(1500.0 + 700 * t, 4.0 * t - 8, 8.0, 0.2, 4)])
@@ -357,10 +358,15 @@ def test_host_pipeline_equals_single_trials(gpu_lib):
             fd.fdas_search_host(plan, np.ascontiguousarray(xs[t]), 1, o, c)
             single.append((int(c[0]), o[:c[0]].tobytes()))
         pinned = torch.from_numpy(xs.ravel().copy()).pin_memory()
-        for src in (pinned.numpy(), np.ascontiguousarray(xs.ravel())):
+        d_all = torch.from_numpy(xs.ravel().copy()).to(DEV)
+        torch.cuda.synchronize()
+        for src in (pinned.numpy(), np.ascontiguousarray(xs.ravel()), d_all):
             out = np.zeros(5 * info.max_cands, dtype=fd.CAND_DTYPE)
             cnt = np.zeros(5, dtype=np.int64)
-            fd.fdas_search_host(plan, src, 5, out, cnt)
+            if isinstance(src, torch.Tensor):   # device series: fdas_search
+                fd.fdas_search(plan, src, 5, out, cnt)
+            else:
+                fd.fdas_search_host(plan, src, 5, out, cnt)
             for t in range(5):
                 got = out[t * info.max_cands: t * info.max_cands + cnt[t]]
                 assert (int(cnt[t]), got.tobytes()) == single[t], t
