@@ -224,11 +224,9 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
     for (int u = 0; u < 16; ++u) y[u] = c2_of(X[tid * X2P + u]);
     float2 out[32];
     dft32_pairs<kInv>(y, out);
+    // every output goes to Ps[n] (room for all L); the valid V start at half_m
 #pragma unroll
-    for (int e = 0; e < 32; ++e) {
-      const int n = tid + NA * brev<32>(e);
-      if (n >= half_m && n < L - half_m) Ps[n - half_m] = cnorm(out[e]);
-    }
+    for (int e = 0; e < 32; ++e) Ps[tid + NA * brev<32>(e)] = cnorm(out[e]);
     __syncthreads();
     // coalesced float4 stores of the plane row slice, its 4-bin maxima and
     // the h = 1 candidates; r = s V + i, i < V, r < nb
@@ -241,7 +239,7 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
     // is completed in L2 before it is written back)
     float* prow = plane ? plane + (size_t)(z >> ib) * (nb << ib) + (r0 << ib) + (z & ib) : nullptr;
     float* qrow = q4 ? q4 + (size_t)z * nq + (r0 >> 2) : nullptr;
-    const float4* P4 = reinterpret_cast<const float4*>(Ps);
+    const float4* P4 = reinterpret_cast<const float4*>(Ps + half_m);  // half_m % 4 == 0
     bool hit = false;
     for (int k = tid; k < n4; k += T) {
       const float4 p4 = P4[k];
