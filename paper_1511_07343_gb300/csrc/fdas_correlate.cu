@@ -257,10 +257,12 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
       if (qrow) qrow[k] = mx;
       hit |= mx >= thr1;
     }
-    if (cands && __syncthreads_or(hit)) {
-      // rare: some power reached T_1; scan the slice again and append
-      for (int k0 = 0; k0 < n4; k0 += T) {
-        const int k = k0 + tid;
+    if (cands && __any_sync(0xffffffffu, hit)) {
+      // rare: some power this warp stored reached T_1; the warp scans its
+      // own float4s again and appends (no CTA barrier: the next pair writes
+      // Ps only after three more)
+      for (int k0 = warp * 32; k0 < n4; k0 += T) {
+        const int k = k0 + (tid & 31);
         const bool in = k < n4;
         const float4 p4 = in ? P4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
         const int rk = (int)(r0 + 4 * k);
@@ -270,7 +272,6 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
         emit(in && p4.w >= thr1, rk + 3, z, 1, p4.w, cands, count, maxc);
       }
     }
-    // the next pair's first shared-memory writes follow three more barriers
   }
   tmem_fence_before_sync();
   __syncthreads();
