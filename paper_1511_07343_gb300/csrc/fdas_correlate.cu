@@ -172,11 +172,11 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
 #pragma unroll
     for (int b = 0; b < 16; ++b) v[b] = c2_of(__ldg(tz + b * RA2 * 16));
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float f[16];
-      tmem_ld16(tbase + 16 * q, f);
+    for (int q = 0; q < 4; q += 2) {
+      float f[32];
+      tmem_ld16x2(tbase + 16 * q, tbase + 16 * q + 16, f);
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 8; ++i)
         v[q * 4 + i] = c2_mul(v[q * 4 + i], c2{make_float2(f[4 * i], f[4 * i + 1]),
                                               make_float2(f[4 * i + 2], f[4 * i + 3])});
     }
