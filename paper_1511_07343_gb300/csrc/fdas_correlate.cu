@@ -62,8 +62,10 @@ __host__ __device__ constexpr int pk_ra2() { return L / 512; }
 //        16/RA2 packed butterflies (u, c) per thread
 //   B  radix-32 over k1 -> c[n2 + NA n1]     thread n2
 // All butterflies work on packed f32x2 pairs (two transforms per FP32
-// instruction). Two shared-memory exchanges per pair; the segment spectrum
-// and the thread's B-stage twiddles live in tensor memory for the whole
+// instruction). Two shared-memory exchanges per pair and three CTA barriers
+// (A1 -> A2, A2 -> B, and B's reads done before the next pair's A1 writes);
+// the segment spectrum and the thread's B-stage twiddles live in tensor
+// memory for the whole
 // sweep over templates; template spectra stream from L2. Besides the plane
 // row the kernel writes the 4-bin maxima Q4[z][r/4] (used to screen the
 // harmonic sums) and emits the h = 1 candidates. Each CTA takes an evenly
@@ -75,14 +77,21 @@ struct Corr {
   static constexpr int RA2 = NA / 16;
   static constexpr int NB2 = 16 / RA2;
   static constexpr int NW = T / 32;
-  static constexpr int X2P = 17;  // float4 pitch of an n2 row in the A2 -> B exchange
-  static constexpr int XF4 = (L / 2 > NA * X2P) ? L / 2 : NA * X2P;
+  static constexpr int XF4 = L / 2;  // the exchange buffer: L/2 packed pairs
   static constexpr int NGROUPS = (NW + 3) / 4;  // warps w and w + 4 share TMEM lanes
   static constexpr int NCOLS = 128 * NGROUPS;   // per thread: 64 (F) + 64 (B twiddles)
   static constexpr int MAXCTA = 512 / NCOLS;
   static constexpr int MINB = L == 8192 ? 2 : 4;
   static constexpr size_t SMEM = 16 * (size_t)(XF4 + RA2 * 16) + 4 * (size_t)L;
 };
+
+// Exchange-buffer slot of row r, packed pair u: 16 float4 per row, the pair
+// index XOR-swizzled by r % 8 so that 8 lanes reading one column of 8
+// consecutive rows, or 8 consecutive columns of one row, hit distinct banks.
+// Rows are r = 16 a + c (A1 -> A2, a over the A2 radix) and n2 = c + 16 d
+// (A2 -> B): A2 thread (u, c) reads rows {16 a + c} and writes its outputs d
+// into rows {16 d + c}, the same slots, so it needs no barrier in between.
+FDAS_DEV int xsw(int r, int u) { return r * 16 + (u ^ (r & 7)); }
 
 FDAS_DEV c2 c2_of(float4 v) { return c2{make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
 FDAS_DEV float4 f4_of(c2 v) { return make_float4(v.re.x, v.re.y, v.im.x, v.im.y); }
@@ -95,7 +104,7 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
                       fdas_cand* __restrict__ cands, unsigned long long* count, int64_t maxc) {
   constexpr int ib = IB;
   using C = Corr<L>;
-  constexpr int T = C::T, NA = C::NA, RA2 = C::RA2, NB2 = C::NB2, X2P = C::X2P;
+  constexpr int T = C::T, NA = C::NA, RA2 = C::RA2, NB2 = C::NB2;
   constexpr int L2 = L / 2;
   extern __shared__ float4 smem4[];
   float4* X = smem4;
@@ -187,7 +196,7 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
       v[brev<16>(c)] = c2_mul_cs(v[brev<16>(c)], make_float2(tw.x, tw.y), make_float2(tw.z, tw.w));
     }
 #pragma unroll
-    for (int c = 0; c < 16; ++c) X[(a1 * 16 + c) * 16 + u1] = f4_of(v[brev<16>(c)]);
+    for (int c = 0; c < 16; ++c) X[xsw(a1 * 16 + c, u1)] = f4_of(v[brev<16>(c)]);
     __syncthreads();
     // ---- A2
     c2 w[NB2][RA2];
@@ -196,9 +205,9 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
       const int g = tid + T * i;
       const int u = g & 15, c = g >> 4;
 #pragma unroll
-      for (int a = 0; a < RA2; ++a) w[i][a] = c2_of(X[(a * 16 + c) * 16 + u]);
+      for (int a = 0; a < RA2; ++a) w[i][a] = c2_of(X[xsw(a * 16 + c, u)]);
     }
-    __syncthreads();
+    // (no barrier: each thread writes its results into the slots it read)
 #pragma unroll
     for (int i = 0; i < NB2; ++i) {
       dft2_brev<RA2, kInv>(w[i]);
@@ -213,7 +222,7 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
           const int d = d0 + dd;
           const c2 t = c2_mul_cs(w[i][brev<RA2>(d)], make_float2(f[4 * dd], f[4 * dd + 1]),
                                  make_float2(f[4 * dd + 2], f[4 * dd + 3]));
-          X[(c + 16 * d) * X2P + u] = f4_of(t);
+          X[xsw(16 * d + c, u)] = f4_of(t);
         }
       }
     }
@@ -221,51 +230,65 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
     // ---- B
     c2 y[16];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) y[u] = c2_of(X[tid * X2P + u]);
+    for (int u = 0; u < 16; ++u) y[u] = c2_of(X[xsw(tid, u)]);
+    // every warp has read X: the next pair's A1 may overwrite it
+    __syncthreads();
     float2 out[32];
     dft32_pairs<kInv>(y, out);
     // every output goes to Ps[n] (room for all L); the valid V start at half_m
 #pragma unroll
     for (int e = 0; e < 32; ++e) Ps[tid + NA * brev<32>(e)] = cnorm(out[e]);
-    __syncthreads();
+    // Outputs n .. n+3 (n % 4 == 0) come from threads n % NA .. +3, lanes of
+    // one warp; so each warp stores the float4s its own lanes produced and a
+    // warp barrier suffices (the next pair writes Ps only after its first
+    // CTA barrier, which every warp reaches after this output stage).
+    __syncwarp();
     // coalesced float4 stores of the plane row slice, its 4-bin maxima and
     // the h = 1 candidates; r = s V + i, i < V, r < nb
     const int64_t r0 = (int64_t)s * V;
     int64_t nvalid = nb - r0;
     if (nvalid > V) nvalid = V;
-    const int n4 = (int)(nvalid >> 2);
+    const int nhi = half_m + (int)nvalid;  // valid outputs n in [half_m, nhi), multiples of 4 apart
     // (half-bin planes, ib = 1: template row z = 2j + e fills columns 2r + e
     // of plane row j; rows 2j and 2j+1 are consecutive pairs, so each sector
     // is completed in L2 before it is written back)
     float* prow = plane ? plane + (size_t)(z >> ib) * (nb << ib) + (r0 << ib) + (z & ib) : nullptr;
     float* qrow = q4 ? q4 + (size_t)z * nq + (r0 >> 2) : nullptr;
-    const float4* P4 = reinterpret_cast<const float4*>(Ps + half_m);  // half_m % 4 == 0
+    const float4* P4 = reinterpret_cast<const float4*>(Ps);
+    const int lane = tid & 31;
+    // lane: 4 outputs starting at n = NA j + 32 warp + 4 (lane % 8), j = lane / 8 + 4 i
+    const int nw = 32 * warp + 4 * (lane & 7);
     bool hit = false;
-    for (int k = tid; k < n4; k += T) {
-      const float4 p4 = P4[k];
-      const float mx = fmaxf(fmaxf(p4.x, p4.y), fmaxf(p4.z, p4.w));
-      if (prow) {
-        if constexpr (IB) {
-          prow[8 * k] = p4.x;
-          prow[8 * k + 2] = p4.y;
-          prow[8 * k + 4] = p4.z;
-          prow[8 * k + 6] = p4.w;
-        } else {
-          reinterpret_cast<float4*>(prow)[k] = p4;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int n = NA * ((lane >> 3) + 4 * i) + nw;
+      if (n >= half_m && n < nhi) {
+        const float4 p4 = P4[n >> 2];
+        const int k = (n - half_m) >> 2;  // float4 index in the row slice
+        const float mx = fmaxf(fmaxf(p4.x, p4.y), fmaxf(p4.z, p4.w));
+        if (prow) {
+          if constexpr (IB) {
+            prow[8 * k] = p4.x;
+            prow[8 * k + 2] = p4.y;
+            prow[8 * k + 4] = p4.z;
+            prow[8 * k + 6] = p4.w;
+          } else {
+            reinterpret_cast<float4*>(prow)[k] = p4;
+          }
         }
+        if (qrow) qrow[k] = mx;
+        hit |= mx >= thr1;
       }
-      if (qrow) qrow[k] = mx;
-      hit |= mx >= thr1;
     }
     if (cands && __any_sync(0xffffffffu, hit)) {
       // rare: some power this warp stored reached T_1; the warp scans its
-      // own float4s again and appends (no CTA barrier: the next pair writes
-      // Ps only after three more)
-      for (int k0 = warp * 32; k0 < n4; k0 += T) {
-        const int k = k0 + (tid & 31);
-        const bool in = k < n4;
-        const float4 p4 = in ? P4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const int rk = (int)(r0 + 4 * k);
+      // own float4s again and appends
+#pragma unroll 1
+      for (int i = 0; i < 8; ++i) {
+        const int n = NA * ((lane >> 3) + 4 * i) + nw;
+        const bool in = n >= half_m && n < nhi;
+        const float4 p4 = in ? P4[n >> 2] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int rk = (int)(r0 + (n - half_m));
         emit(in && rk >= 1 && p4.x >= thr1, rk, z, 1, p4.x, cands, count, maxc);
         emit(in && p4.y >= thr1, rk + 1, z, 1, p4.y, cands, count, maxc);
         emit(in && p4.z >= thr1, rk + 2, z, 1, p4.z, cands, count, maxc);
