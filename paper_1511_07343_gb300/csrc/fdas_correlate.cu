@@ -82,7 +82,7 @@ struct Corr {
   static constexpr int NCOLS = 128 * NGROUPS;   // per thread: 64 (F) + 64 (B twiddles)
   static constexpr int MAXCTA = 512 / NCOLS;
   static constexpr int MINB = L == 8192 ? 2 : 4;
-  static constexpr size_t SMEM = 16 * (size_t)(XF4 + RA2 * 16) + 4 * (size_t)L;
+  static constexpr size_t SMEM = 16 * (size_t)(XF4 + RA2 * 17) + 4 * (size_t)L;
 };
 
 // Exchange-buffer slot of row r, packed pair u: 16 float4 per row, the pair
@@ -108,13 +108,15 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
   constexpr int L2 = L / 2;
   extern __shared__ float4 smem4[];
   float4* X = smem4;
-  float4* twA = smem4 + C::XF4;  // (c, c, s, s) of exp(+2 pi i a c / NA), a < RA2, c < 16
-  float* Ps = reinterpret_cast<float*>(twA + RA2 * 16);
+  // (c, c, s, s) of exp(+2 pi i a c / NA), a < RA2, c < 16, at a * 17 + c: a
+  // warp reads two rows a at once, which the padding puts on other banks
+  float4* twA = smem4 + C::XF4;
+  float* Ps = reinterpret_cast<float*>(twA + RA2 * 17);
   __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int e = tid; e < RA2 * 16; e += T) {
     const float2 w = cconj(__ldg(twL + (((e >> 4) * (e & 15) * 32) & (L - 1))));
-    twA[e] = make_float4(w.x, w.x, w.y, w.y);
+    twA[(e >> 4) * 17 + (e & 15)] = make_float4(w.x, w.x, w.y, w.y);
   }
   if (warp == 0) {
     tmem_alloc(&s_tmem, C::NCOLS);
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
     dft2_brev<16, kInv>(v);
 #pragma unroll
     for (int c = 1; c < 16; ++c) {
-      const float4 tw = twA[a1 * 16 + c];
+      const float4 tw = twA[a1 * 17 + c];
       v[brev<16>(c)] = c2_mul_cs(v[brev<16>(c)], make_float2(tw.x, tw.y), make_float2(tw.z, tw.w));
     }
 #pragma unroll
