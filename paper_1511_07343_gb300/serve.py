@@ -34,6 +34,42 @@ from . import fdas
 DEFAULT_CLASSES = {50: (128, 2048), 100: (256, 4096), 200: (512, 8192)}
 
 
+def plan_footprint(n_max: int, zmax: int, m: int, L: int, dz: int = 2,
+                   max_cands: int = 1 << 20) -> int:
+    """Device bytes a plan of this class holds, for admission: plane and its
+    4-bin maxima, spectra and workspaces, segment spectra, templates and the
+    candidate list (an upper estimate of fdas_plan_get_info's device_bytes)."""
+    Z = 2 * (zmax // dz) + 1
+    nb = n_max // 2
+    S = (nb + (L - m) - 1) // (L - m)
+    core = (4 * Z * nb + Z * nb + 8 * 4 * nb + 8 * S * L + 24 * Z * L
+            + 16 * max_cands + 4 * n_max)
+    # twiddle tables and counters (a few MB at most), plus 2% headroom
+    return int(core * 1.02) + (8 << 20)
+
+
+class Budget:
+    """Thread-safe reservation of a fixed number of device bytes."""
+
+    def __init__(self, total: int):
+        self.total = int(total)
+        self.reserved = 0
+        self._lock = threading.Lock()
+
+    def try_reserve(self, nbytes: int) -> bool:
+        with self._lock:
+            if self.reserved + nbytes > self.total:
+                return False
+            self.reserved += nbytes
+            return True
+
+    def release(self, nbytes: int):
+        with self._lock:
+            if nbytes > self.reserved:
+                raise ValueError("release of bytes never reserved")
+            self.reserved -= nbytes
+
+
 @dataclasses.dataclass
 class Result:
     candidates: np.ndarray      # fdas.CAND_DTYPE, sorted by (h, r_top, z_idx)
@@ -70,7 +106,7 @@ class Server:
             free, _ = torch.cuda.mem_get_info(self.device)
             hbm_budget = int(0.8 * free)
         self.hbm_budget = int(hbm_budget)
-        self._reserved = 0
+        self._budget = Budget(self.hbm_budget)
         self._lock = threading.Lock()
         self._queue: "queue.Queue[_Request | None]" = queue.Queue()
         self._slots = [_Slot(self, i) for i in range(n_slots)]
@@ -116,23 +152,13 @@ class Server:
     # -- admission ------------------------------------------------------------
     def _footprint(self, zmax: int) -> int:
         m, L = self.classes[zmax]
-        Z = 2 * (zmax // self.dz) + 1
-        nb = self.n_max // 2
-        S = (nb + (L - m) - 1) // (L - m)
-        # plane + 4-bin maxima + spectra + segments + templates + candidates
-        return (4 * Z * nb + Z * nb + 8 * 4 * nb + 8 * S * L + 24 * Z * L
-                + 16 * self.max_cands + 4 * self.n_max)
+        return plan_footprint(self.n_max, zmax, m, L, self.dz, self.max_cands)
 
     def _try_reserve(self, nbytes: int) -> bool:
-        with self._lock:
-            if self._reserved + nbytes > self.hbm_budget:
-                return False
-            self._reserved += nbytes
-            return True
+        return self._budget.try_reserve(nbytes)
 
     def _release(self, nbytes: int):
-        with self._lock:
-            self._reserved -= nbytes
+        self._budget.release(nbytes)
 
 
 class _Slot(threading.Thread):

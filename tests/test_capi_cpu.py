@@ -96,3 +96,38 @@ def test_plan_create_accepts_235_lengths(lib, N):
     with pytest.raises(lib.FdasError) as e:
         lib.fdas_plan_create(N, 20, 2, 64, 2048, 4, 6.0, 100)
     assert e.value.status in (lib.FDAS_ERR_NOMEM, lib.FDAS_ERR_CUDA)
+
+
+def test_newer_entry_points_reject_null_and_bad_arguments(lib):
+    """Argument checks of the later entry points run before any device work."""
+    import ctypes
+    so = lib.load()
+    INV = lib.FDAS_ERR_INVALID
+    assert so.fdas_plan_set_correlation(None, 1) == INV
+    assert so.fdas_plan_set_whitening(None, 1) == INV
+    assert so.fdas_plan_set_interbin(None, 1) == INV
+    assert so.fdas_distill(None, None, None, None, None) == INV
+    assert so.fdas_batch_set_graphs(None, 1) == INV
+    assert so.fdas_batch_get_info(None, None) == INV
+    assert so.fdas_search_batch(None, None, None, 1, None, None) == INV
+    assert so.fdas_batch_destroy(None) == lib.FDAS_OK
+    out = ctypes.c_void_p()
+    assert so.fdas_batch_create_tuned(None, 1 << 14, 20, 2, 64, 4, 6.0, 16, None, None) == INV
+    # an impossible length fails before the tuner touches the device
+    assert so.fdas_batch_create_tuned(ctypes.byref(out), 3000, 20, 2, 64, 4, 6.0, 16, None,
+                                      None) == INV
+    assert out.value is None
+    assert so.fdas_spectrum_noalloc(None, 1 << 14, None, None) == INV
+    assert so.fdas_stage_plane(None, None, None) == INV
+
+
+def test_binding_dtypes_match_the_c_structs(lib):
+    """The numpy record types and ctypes structures mirror fdas.h."""
+    assert lib.CAND_DTYPE.itemsize == 16
+    assert lib.PEAK_DTYPE.itemsize == 24
+    assert list(lib.PEAK_DTYPE.names) == ["r_top", "z_idx", "h", "power", "sigma", "log10_p"]
+    import ctypes
+    assert ctypes.sizeof(lib.fdas_batch_info) == 8 + 4 * 4 + 8 * 2 + 4 * 4 + 4 * 4
+    src = open(os.path.join(ROOT, "include", "fdas.h")).read()
+    for field in ("r_top", "z_idx", "power", "sigma", "log10_p", "graph_builds", "tuned_ms"):
+        assert field in src

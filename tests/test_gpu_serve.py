@@ -67,3 +67,17 @@ def test_memory_budget_limits_plans(gpu_lib):
         futs = [srv.submit(x, (20, 40)[i % 2]) for i, x in enumerate(xs)]
         res = [f.result(timeout=300) for f in futs]
     assert all(r.count > 0 for r in res)
+
+
+def test_footprint_estimate_bounds_the_plans_device_bytes(gpu_lib):
+    from paper_1511_07343_gb300.serve import plan_footprint
+    fd = gpu_lib
+    stream = torch.cuda.current_stream(DEV).cuda_stream
+    for zmax, (m, L) in {50: (128, 2048), 200: (512, 8192)}.items():
+        plan = fd.fdas_plan_create(1 << 20, zmax, 2, m, L, 16, 6.0, 1 << 16, stream)
+        try:
+            info = fd.fdas_plan_get_info(plan)
+        finally:
+            fd.fdas_plan_destroy(plan)
+        est = plan_footprint(1 << 20, zmax, m, L, 2, 1 << 16)
+        assert info.device_bytes <= est <= 1.5 * info.device_bytes, (zmax, info.device_bytes, est)
