@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (derivations in the design doc):
+Tolerances (each follows from the float32 arithmetic of its stage):
   * template taps: float64 on both sides, |d tau| <= 1e-12;
   * template spectra (float32 store of a float64 DFT): <= 2e-7 * max |T|;
   * spectrum (float32 FFT of length N): max |dX| <= 2e-5 * rms(X);
