@@ -288,7 +288,9 @@ def batch_measure(fdas, dev, n_trials=256, reps=2, seed=3):
     return {"trials": n_trials, "N_min": min(lens), "N_max": max(lens),
             "distinct_N": len(set(lens)), "zmax": 200, "template_width": 512,
             "segment": info.segment,
+            "harmsum_block": info.hs_block,
             "tuner": {"segments": list(info.tuned_segment[:info.n_tuned]),
+                      "harmsum_blocks": list(info.tuned_hs_block[:info.n_tuned]),
                       "trial_ms_at_N_max": [round(v, 4) for v in info.tuned_ms[:info.n_tuned]],
                       "seconds": tune_s},
             "graph": {"value": n_trials * 1e3 / g_ms, "unit": "trials/s", "ms_per_batch": g_ms,

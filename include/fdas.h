@@ -144,27 +144,31 @@ int fdas_search_batch(fdas_batch* batch, const float* const* d_series, const int
  * fdas_batch_set_graphs(batch, 0) launches the kernels directly instead. */
 int fdas_batch_set_graphs(fdas_batch* batch, int32_t enable);
 
-/* Autotuned batch: times one trial of every segment length L in
- * {2048, 4096, 8192} with L >= 2m on a probe series of N_max samples
- * (d_probe, device; NULL = seeded Gaussian white noise made on the device),
- * each on a fresh plan (median of 3 after a warm-up), and creates the batch
- * with the fastest. L sets the segment FFT size, the number of segments and
- * the correlation kernel's occupancy; the plane is the same up to float32
- * rounding for every L. Other arguments as fdas_batch_create. */
+/* Autotuned batch: times one trial of every combination of segment length
+ * L in {2048, 4096, 8192} with L >= 2m and harmonic-sum block of 256 or 128
+ * threads (16384 or 8192 top bins per block) on a probe series of N_max
+ * samples (d_probe, device; NULL = seeded Gaussian white noise made on the
+ * device), on a fresh plan per L (median of 3 after a warm-up), and creates
+ * the batch with the fastest. L sets the segment FFT size, the number of
+ * segments and the correlation kernel's occupancy; the plane is the same up
+ * to float32 rounding for every L, and the candidates do not depend on the
+ * block size. Other arguments as fdas_batch_create. */
 int fdas_batch_create_tuned(fdas_batch** out, int64_t N_max, int32_t zmax, int32_t dz,
                             int32_t template_width, int32_t nharm, float sigma,
                             int64_t max_cands, const float* d_probe, void* stream);
 
 typedef struct {
   int64_t N_max;
-  int32_t segment;          /* L in use */
-  int32_t n_lengths;        /* distinct series lengths with a geometry */
-  int32_t graphs;           /* 1 when batches run as captured CUDA graphs */
-  int32_t n_tuned;          /* segment lengths the autotuner timed (0: not tuned) */
-  int64_t graph_builds;     /* captures made */
-  int64_t graph_launches;   /* graph launches */
-  int32_t tuned_segment[4]; /* the lengths timed ... */
-  float tuned_ms[4];        /* ... and their median trial times (ms) */
+  int32_t segment;           /* L in use */
+  int32_t n_lengths;         /* distinct series lengths with a geometry */
+  int32_t graphs;            /* 1 when batches run as captured CUDA graphs */
+  int32_t n_tuned;           /* configurations the autotuner timed (0: not tuned) */
+  int64_t graph_builds;      /* captures made */
+  int64_t graph_launches;    /* graph launches */
+  int32_t hs_block;          /* harmonic-sum block in use (threads) */
+  int32_t tuned_segment[8];  /* the configurations timed: L ... */
+  int32_t tuned_hs_block[8]; /* ... harmonic-sum block ... */
+  float tuned_ms[8];         /* ... and their median trial times (ms) */
 } fdas_batch_info;
 int fdas_batch_get_info(const fdas_batch* batch, fdas_batch_info* info);
 

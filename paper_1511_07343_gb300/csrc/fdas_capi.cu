@@ -659,8 +659,9 @@ struct fdas_batch {
   int64_t graph_builds = 0, graph_launches = 0;
   // autotuner record
   int n_tuned = 0;
-  int32_t tuned_segment[4] = {0, 0, 0, 0};
-  float tuned_ms[4] = {0, 0, 0, 0};
+  int32_t tuned_segment[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int32_t tuned_hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  float tuned_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -692,33 +693,36 @@ int batch_view(fdas_batch* b, int64_t N, fdas_plan** out) {
   return FDAS_OK;
 }
 
-// Median time of one trial (3 timed after 1 warm-up) of a fresh plan with
-// segment length L on the probe series.
+// Median times of one trial (3 timed after 1 warm-up) of a fresh plan with
+// segment length L on the probe series, for each harmonic-sum block size in
+// hs[0..nhs).
 int time_segment(int64_t N, int32_t zmax, int32_t dz, int32_t m, int32_t L, int32_t nharm,
                  float sigma, int64_t max_cands, const float* d_probe, cudaStream_t s,
-                 float* ms_out) {
+                 const int* hs, int nhs, float* ms_out) {
   fdas_plan* p = nullptr;
   int rc = fdas_plan_create(&p, N, zmax, dz, m, L, nharm, sigma, max_cands, s);
   if (rc) return rc;
-  cudaEvent_t ev[4];
+  cudaEvent_t ev[2];
   int made = 0;
-  for (; made < 4 && !rc; ++made)
+  for (; made < 2 && !rc; ++made)
     if (cudaEventCreate(&ev[made]) != cudaSuccess) rc = set_error(FDAS_ERR_CUDA, "cudaEventCreate failed");
-  float t[3] = {0, 0, 0};
-  if (!rc) rc = run_trial(p, d_probe, p->cands, p->count);
-  for (int i = 0; i < 3 && !rc; ++i) {
-    rc = cuda_check(cudaEventRecord(ev[0], s), "event");
-    if (!rc) rc = run_trial(p, d_probe, p->cands, p->count);
-    if (!rc) rc = cuda_check(cudaEventRecord(ev[1], s), "event");
-    if (!rc) rc = cuda_check(cudaEventSynchronize(ev[1]), "event sync");
-    if (!rc) rc = cuda_check(cudaEventElapsedTime(&t[i], ev[0], ev[1]), "elapsed");
+  for (int c = 0; c < nhs && !rc; ++c) {
+    p->hs_threads = hs[c];
+    float t[3] = {0, 0, 0};
+    rc = run_trial(p, d_probe, p->cands, p->count);
+    for (int i = 0; i < 3 && !rc; ++i) {
+      rc = cuda_check(cudaEventRecord(ev[0], s), "event");
+      if (!rc) rc = run_trial(p, d_probe, p->cands, p->count);
+      if (!rc) rc = cuda_check(cudaEventRecord(ev[1], s), "event");
+      if (!rc) rc = cuda_check(cudaEventSynchronize(ev[1]), "event sync");
+      if (!rc) rc = cuda_check(cudaEventElapsedTime(&t[i], ev[0], ev[1]), "elapsed");
+    }
+    std::sort(t, t + 3);
+    ms_out[c] = t[1];
   }
   for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
   fdas_plan_destroy(p);
-  if (rc) return rc;
-  std::sort(t, t + 3);
-  *ms_out = t[1];
-  return FDAS_OK;
+  return rc;
 }
 
 // Trials of a batch in order, launched directly on the plan's stream.
@@ -766,16 +770,20 @@ int fdas_batch_create_tuned(fdas_batch** out, int64_t N_max, int32_t zmax, int32
     rc = launch_probe_noise(own, N_max, 0x5eedull, s);
     d_probe = own;
   }
+  const int hs[2] = {256, 128};  // harmonic-sum block sizes
   int n = 0, best = -1;
-  int32_t Ls[4] = {0, 0, 0, 0};
-  float ms[4] = {0, 0, 0, 0};
+  int32_t Ls[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  float ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int i = 0; i < 3 && !rc; ++i) {
     if (cand[i] < 2 * m) continue;
-    rc = time_segment(N_max, zmax, dz, m, cand[i], nharm, sigma, max_cands, d_probe, s, &ms[n]);
+    rc = time_segment(N_max, zmax, dz, m, cand[i], nharm, sigma, max_cands, d_probe, s, hs, 2,
+                      &ms[n]);
     if (rc) break;
-    Ls[n] = cand[i];
-    if (best < 0 || ms[n] < ms[best]) best = n;
-    ++n;
+    for (int c = 0; c < 2; ++c, ++n) {
+      Ls[n] = cand[i];
+      Hs[n] = hs[c];
+      if (best < 0 || ms[n] < ms[best]) best = n;
+    }
   }
   if (own) {
     cudaStreamSynchronize(s);
@@ -785,9 +793,11 @@ int fdas_batch_create_tuned(fdas_batch** out, int64_t N_max, int32_t zmax, int32
   if (best < 0) return set_error(FDAS_ERR_INVALID, "no segment length with L >= 2m");
   rc = fdas_batch_create(out, N_max, zmax, dz, m, Ls[best], nharm, sigma, max_cands, stream);
   if (rc) return rc;
+  (*out)->base->hs_threads = Hs[best];
   (*out)->n_tuned = n;
   for (int i = 0; i < n; ++i) {
     (*out)->tuned_segment[i] = Ls[i];
+    (*out)->tuned_hs[i] = Hs[i];
     (*out)->tuned_ms[i] = ms[i];
   }
   return FDAS_OK;
@@ -808,9 +818,11 @@ int fdas_batch_get_info(const fdas_batch* b, fdas_batch_info* info) {
   info->graphs = b->graphs && b->base->stream != nullptr;
   info->graph_builds = b->graph_builds;
   info->graph_launches = b->graph_launches;
+  info->hs_block = b->base->hs_threads;
   info->n_tuned = b->n_tuned;
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 8; ++i) {
     info->tuned_segment[i] = b->tuned_segment[i];
+    info->tuned_hs_block[i] = b->tuned_hs[i];
     info->tuned_ms[i] = b->tuned_ms[i];
   }
   return FDAS_OK;

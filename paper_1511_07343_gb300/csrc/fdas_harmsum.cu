@@ -76,13 +76,13 @@ __host__ __device__ constexpr int class_stride(int q) {
   return 32 * (q >> ctz5(q)) + (32 >> ctz5(q));
 }
 
-constexpr int kHsThreads = 256;
-constexpr int kHsWarps = kHsThreads / 32;
+// a block is NT threads (128 or 256: the harmonic-sum tiling the batch
+// autotuner chooses), each warp independent of the others
 constexpr int kHsCells = 64;
-constexpr int kHsSpan = kHsThreads * kHsCells;
 constexpr int kWarpSpan = 32 * kHsCells;
 constexpr int kStageW = 16 * 34;  // largest staged slice per warp (q = 16), floats
-constexpr size_t kHsSmem = (size_t)3 * kStageW * kHsWarps * sizeof(float);
+template <int NT>
+constexpr size_t hs_smem() { return (size_t)3 * kStageW * (NT / 32) * sizeof(float); }
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
@@ -189,8 +189,8 @@ FDAS_DEV void hs_steps(const HsCtx& x, float2 (&acc)[kHsCells / 4], unsigned& pm
   }
 }
 
-template <int NLEV>
-__global__ void __launch_bounds__(kHsThreads) k_harmsum_staged(
+template <int NLEV, int NT>
+__global__ void __launch_bounds__(NT) k_harmsum_staged(
     const float* __restrict__ P, const float* __restrict__ Q4, int64_t nb, int Z, Thr thr,
     fdas_cand* __restrict__ out, unsigned long long* count, int64_t maxc) {
   constexpr int NQ = 1 << (NLEV - 1);
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kHsThreads) k_harmsum_staged(
   x.stage = stage + warp * 3 * kStageW;
   x.Q4 = Q4;
   x.nq = nb >> 2;
-  x.R0w = (int64_t)blockIdx.x * kHsSpan + (int64_t)kWarpSpan * warp;
+  x.R0w = (int64_t)blockIdx.x * (NT * kHsCells) + (int64_t)kWarpSpan * warp;
   x.lane = threadIdx.x & 31;
   x.zc = (Z - 1) / 2;
   const int jc = j - x.zc;
@@ -269,42 +269,46 @@ int launch_pool4(fdas_plan* p, const float* d_plane, float* d_q4, fdas_cand* d_o
   return cuda_check(cudaGetLastError(), "k_pool4");
 }
 
+namespace {
+
+template <int NLEV, int NT>
+int hs_launch(fdas_plan* p, const float* d_plane, const float* d_q4, fdas_cand* d_out,
+              unsigned long long* d_count) {
+  static int attr_dev = -1;  // the shared-memory attribute, set once per device
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_check(e, "cudaGetDevice");
+  if (attr_dev != dev) {
+    e = cudaFuncSetAttribute(k_harmsum_staged<NLEV, NT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs_smem<NT>());
+    if (e != cudaSuccess) return cuda_check(e, "k_harmsum_staged attr");
+    attr_dev = dev;
+  }
+  const int64_t w = plane_width(p);
+  dim3 grid((unsigned)((w + NT * kHsCells - 1) / (NT * kHsCells)), p->Z);
+  k_harmsum_staged<NLEV, NT><<<grid, NT, hs_smem<NT>(), p->stream>>>(
+      d_plane, d_q4, w, p->Z, thresholds_of(p), d_out, d_count, p->max_cands);
+  return cuda_check(cudaGetLastError(), "k_harmsum_staged");
+}
+
+template <int NT>
+int hs_dispatch(fdas_plan* p, const float* d_plane, const float* d_q4, fdas_cand* d_out,
+                unsigned long long* d_count) {
+  switch (p->n_levels) {
+    case 2: return hs_launch<2, NT>(p, d_plane, d_q4, d_out, d_count);
+    case 3: return hs_launch<3, NT>(p, d_plane, d_q4, d_out, d_count);
+    case 4: return hs_launch<4, NT>(p, d_plane, d_q4, d_out, d_count);
+    default: return hs_launch<5, NT>(p, d_plane, d_q4, d_out, d_count);
+  }
+}
+
+}  // namespace
+
 int launch_harmsum(fdas_plan* p, const float* d_plane, const float* d_q4, fdas_cand* d_out,
                    unsigned long long* d_count) {
   if (p->n_levels < 2) return FDAS_OK;
-  const int64_t w = plane_width(p);
-  dim3 grid((unsigned)((w + kHsSpan - 1) / kHsSpan), p->Z);
-  const Thr thr = thresholds_of(p);
-  static bool attr_set[6] = {false, false, false, false, false, false};
-  if (!attr_set[p->n_levels]) {
-    cudaError_t e = cudaSuccess;
-    switch (p->n_levels) {
-      case 2: e = cudaFuncSetAttribute(k_harmsum_staged<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHsSmem); break;
-      case 3: e = cudaFuncSetAttribute(k_harmsum_staged<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHsSmem); break;
-      case 4: e = cudaFuncSetAttribute(k_harmsum_staged<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHsSmem); break;
-      default: e = cudaFuncSetAttribute(k_harmsum_staged<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHsSmem); break;
-    }
-    if (e != cudaSuccess) return cuda_check(e, "k_harmsum_staged attr");
-    attr_set[p->n_levels] = true;
-  }
-  switch (p->n_levels) {
-    case 2:
-      k_harmsum_staged<2><<<grid, kHsThreads, kHsSmem, p->stream>>>(d_plane, d_q4, w, p->Z, thr,
-                                                            d_out, d_count, p->max_cands);
-      break;
-    case 3:
-      k_harmsum_staged<3><<<grid, kHsThreads, kHsSmem, p->stream>>>(d_plane, d_q4, w, p->Z, thr,
-                                                            d_out, d_count, p->max_cands);
-      break;
-    case 4:
-      k_harmsum_staged<4><<<grid, kHsThreads, kHsSmem, p->stream>>>(d_plane, d_q4, w, p->Z, thr,
-                                                            d_out, d_count, p->max_cands);
-      break;
-    default:
-      k_harmsum_staged<5><<<grid, kHsThreads, kHsSmem, p->stream>>>(d_plane, d_q4, w, p->Z, thr,
-                                                            d_out, d_count, p->max_cands);
-  }
-  return cuda_check(cudaGetLastError(), "k_harmsum_staged");
+  return p->hs_threads == 128 ? hs_dispatch<128>(p, d_plane, d_q4, d_out, d_count)
+                              : hs_dispatch<256>(p, d_plane, d_q4, d_out, d_count);
 }
 
 }  // namespace fdas

@@ -49,6 +49,7 @@ struct fdas_plan {
   // tensor-core correlation (precision variant); corr_mode = FDAS_CORR_*
   int corr_mode = 0;
   int whiten_mode = 0;         // FDAS_WHITEN_*
+  int hs_threads = 256;        // harmonic-sum block (128 or 256 threads)
   // half-bin planes: taps and spectra of 2Z template rows (row 2j + e at
   // frequency offset e/2); the plane and Q4 then have 2 nb columns
   int interbin = 0;

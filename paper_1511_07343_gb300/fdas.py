@@ -47,8 +47,9 @@ class fdas_batch_info(ctypes.Structure):
     _fields_ = [("N_max", ctypes.c_int64), ("segment", ctypes.c_int32),
                 ("n_lengths", ctypes.c_int32), ("graphs", ctypes.c_int32),
                 ("n_tuned", ctypes.c_int32), ("graph_builds", ctypes.c_int64),
-                ("graph_launches", ctypes.c_int64), ("tuned_segment", ctypes.c_int32 * 4),
-                ("tuned_ms", ctypes.c_float * 4)]
+                ("graph_launches", ctypes.c_int64), ("hs_block", ctypes.c_int32),
+                ("tuned_segment", ctypes.c_int32 * 8), ("tuned_hs_block", ctypes.c_int32 * 8),
+                ("tuned_ms", ctypes.c_float * 8)]
 
 
 CAND_DTYPE = np.dtype([("r_top", "<i4"), ("z_idx", "<i4"), ("h", "<i4"), ("power", "<f4")])

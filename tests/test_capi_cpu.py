@@ -127,7 +127,7 @@ def test_binding_dtypes_match_the_c_structs(lib):
     assert lib.PEAK_DTYPE.itemsize == 24
     assert list(lib.PEAK_DTYPE.names) == ["r_top", "z_idx", "h", "power", "sigma", "log10_p"]
     import ctypes
-    assert ctypes.sizeof(lib.fdas_batch_info) == 8 + 4 * 4 + 8 * 2 + 4 * 4 + 4 * 4
+    assert ctypes.sizeof(lib.fdas_batch_info) == 8 + 4 * 4 + 8 * 2 + 4 + 3 * 4 * 8 + 4
     src = open(os.path.join(ROOT, "include", "fdas.h")).read()
     for field in ("r_top", "z_idx", "power", "sigma", "log10_p", "graph_builds", "tuned_ms"):
         assert field in src

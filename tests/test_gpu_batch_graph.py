@@ -89,11 +89,14 @@ def test_tuned_batch_picks_the_fastest_segment(gpu_lib):
     batch = fd.fdas_batch_create_tuned(N_MAX, 40, 2, 128, 4, 6.0, MAXC, None, stream.cuda_stream)
     try:
         info = fd.fdas_batch_get_info(batch)
-        assert info.n_tuned == 3
-        assert list(info.tuned_segment[:3]) == [2048, 4096, 8192]
-        ms = list(info.tuned_ms[:3])
+        assert info.n_tuned == 6
+        assert list(info.tuned_segment[:6]) == [2048, 2048, 4096, 4096, 8192, 8192]
+        assert list(info.tuned_hs_block[:6]) == [256, 128] * 3
+        ms = list(info.tuned_ms[:6])
         assert all(t > 0 for t in ms)
-        assert info.segment == info.tuned_segment[int(np.argmin(ms))]
+        best = int(np.argmin(ms))
+        assert info.segment == info.tuned_segment[best]
+        assert info.hs_block == info.tuned_hs_block[best]
         xs = series_list()
         got = run(fd, batch, xs, stream)
     finally:
@@ -118,8 +121,8 @@ def test_tuner_skips_segments_shorter_than_2m(gpu_lib):
                                        stream.cuda_stream)
     try:
         info = fd.fdas_batch_get_info(batch)
-        assert info.n_tuned == 2
-        assert list(info.tuned_segment[:2]) == [4096, 8192]
+        assert info.n_tuned == 4
+        assert list(info.tuned_segment[:4]) == [4096, 4096, 8192, 8192]
         assert info.segment in (4096, 8192)
     finally:
         fd.fdas_batch_destroy(batch)
