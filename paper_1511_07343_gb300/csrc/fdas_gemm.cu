@@ -55,13 +55,14 @@ namespace {
 constexpr int kGmNT = 512;                     // bins per tile = TMEM columns
 constexpr int kGmMT = 128;                     // left-factor rows per tile = TMEM lanes
 constexpr int kGmKB = 64;                      // K per pipeline stage
-constexpr int kGmStages = 4;
+constexpr int kGmStages = 8;
+constexpr int kGmWBufs = 1;                    // Hankel buffers (the room goes to stages)
 constexpr int kGmStageBytes = kGmMT * kGmKB * 2;  // 16 KB
 constexpr int kGmThreads = 192;
 constexpr uint32_t kGmSpin = 1u << 23;         // polls of one bounded wait (~1 s)
 
-// K section -> shared-memory part (0 Re hi, 1 Im hi, 2 Re lo, 3 Im lo)
-__constant__ int kSecPart[6] = {2, 3, 0, 1, 0, 1};
+// K sections 0..5 read shared-memory parts 2, 3, 0, 1, 0, 1 (0 Re hi, 1 Im hi,
+// 2 Re lo, 3 Im lo)
 
 struct GemmLayout {
   uint32_t w_part, w_buf, w_off, bar_off, total;
@@ -72,8 +73,8 @@ __host__ __device__ inline GemmLayout gemm_layout(int m) {
   g.w_part = (uint32_t)(kGmNT + m) * 16u;
   g.w_buf = 4u * g.w_part;
   g.w_off = kGmStages * kGmStageBytes;
-  g.bar_off = g.w_off + 2u * g.w_buf;
-  g.total = g.bar_off + 128u;  // 13 barriers + TMEM slot + abort flag
+  g.bar_off = g.w_off + kGmWBufs * g.w_buf;
+  g.total = g.bar_off + 256u;  // 2 x kGmStages + 5 barriers, TMEM slot, abort flag
   return g;
 }
 
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(kGmThreads, 1)
     auto build_w = [&](int q) {
       const int64_t r0 = (int64_t)(blockIdx.x + (int64_t)q * gridDim.x) * kGmNT;
       const int64_t base = r0 - m / 2;
-      uint8_t* wp = smem + g.w_off + (size_t)(q & 1) * g.w_buf;
+      uint8_t* wp = smem + g.w_off + (size_t)(q % kGmWBufs) * g.w_buf;
       const int nch = kGmNT + m;
       for (int j = tid; j < nch; j += 128) {
         uint32_t p[4][4];
@@ -342,11 +343,10 @@ __global__ void __launch_bounds__(kGmThreads, 1)
       }
       fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(bar_wfull0 + 8u * (q & 1));
+      if (lane == 0) mbar_arrive(bar_wfull0 + 8u * (q % kGmWBufs));
     };
 
-    if (my_tiles > 0) build_w(0);
-    if (my_tiles > 1) build_w(1);
+    for (int q = 0; q < kGmWBufs && q < my_tiles; ++q) build_w(q);
     const float pscale = 1.f / (E::kScale * E::kScale);
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
     uint32_t tile = 0;
@@ -388,8 +388,8 @@ __global__ void __launch_bounds__(kGmThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(bar_tempty);
       }
-      // the MMAs of bin block q are retired: its W buffer takes block q + 2
-      if (ok && q + 2 < my_tiles) build_w(q + 2);
+      // the MMAs of bin block q are retired: its W buffer takes block q + kGmWBufs
+      if (ok && q + kGmWBufs < my_tiles) build_w(q + kGmWBufs);
     }
   } else if (warp == 4) {
     // ---------------------------------------------- producer
@@ -420,15 +420,22 @@ __global__ void __launch_bounds__(kGmThreads, 1)
       constexpr uint32_t idesc = idesc_f16(E::kBf16, kGmMT, 256);
       uint32_t it = 0, tile = 0;
       bool ok = true;
+      // descriptors advance by adding to their start-address field (16-byte
+      // units): the A stage by 16 per K step, the Hankel part by 1 per bin
+      const uint64_t a_desc0 = sdesc(a_base, 128u, 1024u);
       for (int q = 0; q < my_tiles && ok; ++q) {
-        const uint32_t wb = w_base + (uint32_t)(q & 1) * g.w_buf;
-        if (!mbar_wait(bar_wfull0 + 8u * (q & 1), (uint32_t)(q >> 1) & 1u, abort, status)) break;
+        const uint32_t wb = w_base + (uint32_t)(q % kGmWBufs) * g.w_buf;
+        const uint64_t w_desc0 = sdesc(wb, 128u, 128u);  // part pt at + pt * w_part / 16
+        if (!mbar_wait(bar_wfull0 + 8u * (q % kGmWBufs), (uint32_t)(q / kGmWBufs) & 1u, abort,
+                       status))
+          break;
         for (int mt = 0; mt < nMT && ok; ++mt, ++tile) {
           if (tile > 0 && !mbar_wait(bar_tempty, (tile - 1) & 1u, abort, status)) {
             ok = false;
             break;
           }
           tmem_fence_after_sync();
+          int sec = 0, d0 = 0;  // K section and tap offset of the next K step
           for (int kb = 0; kb < nKB; ++kb, ++it) {
             const int s = it % kGmStages;
             if (!mbar_wait(bar_full(s), (it / kGmStages) & 1u, abort, status)) {
@@ -436,17 +443,19 @@ __global__ void __launch_bounds__(kGmThreads, 1)
               break;
             }
             tmem_fence_after_sync();
-            const uint32_t a_st = a_base + (uint32_t)s * kGmStageBytes;
+            const uint64_t ad = a_desc0 + (uint64_t)((s * kGmStageBytes) >> 4);
 #pragma unroll
             for (int i = 0; i < kGmKB / 16; ++i) {
-              const int k = kb * kGmKB + i * 16;
-              const int sec = k / m, d0 = k - sec * m;
-              const uint64_t ad = sdesc(a_st + (uint32_t)i * 256u, 128u, 1024u);
-              const uint32_t wp = wb + (uint32_t)kSecPart[sec] * g.w_part;
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const uint64_t bd = sdesc(wp + (uint32_t)(h * 256 + d0) * 16u, 128u, 128u);
-                umma(tmem + (uint32_t)(h * 256), ad, bd, idesc, (kb | i) != 0);
+              // sections 0, 1 read parts 2, 3 (lo); 2, 4 part 0; 3, 5 part 1
+              const int pt = sec < 2 ? sec + 2 : (sec & 1);
+              const uint64_t bd = w_desc0 + (uint64_t)(pt * (g.w_part >> 4) + d0);
+              const uint32_t acc = (kb | i) != 0;
+              umma(tmem, ad + 16u * i, bd, idesc, acc);
+              umma(tmem + 256u, ad + 16u * i, bd + 256u, idesc, acc);
+              d0 += 16;
+              if (d0 == m) {
+                d0 = 0;
+                ++sec;
               }
             }
             umma_commit(bar_empty(s));
