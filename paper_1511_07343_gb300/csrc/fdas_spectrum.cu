@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(kNT) k_fft_cols(const float2* __restrict__ z,
                                                   const float2* __restrict__ tw_len,
                                                   const float2* __restrict__ tw_lo,
                                                   const float2* __restrict__ tw_hi, int h4) {
-  __shared__ float2 buf[NB * LEN];
+  extern __shared__ float2 buf[];  // NB * LEN
   const int tid = threadIdx.x;
   const int b0 = blockIdx.x * NB;
   for (int i = tid; i < NB * LEN; i += kNT) {
@@ -85,9 +85,23 @@ __global__ void k_unpack(const float2* __restrict__ Zf, float2* __restrict__ X, 
 
 template <int LEN>
 int launch_cols(fdas_plan* p, const float2* z, float2* T) {
-  constexpr int NB = LEN >= 4096 ? 1 : (LEN >= 2048 ? 2 : 4);
-  k_fft_cols<LEN, NB><<<p->M1 / NB, kNT, 0, p->stream>>>(z, T, p->M1, p->tw_M2, p->tw4_lo,
-                                                           p->tw4_hi, p->h4);
+  // NB columns per CTA: NB consecutive float2 of a row make one 32-byte
+  // sector from NB = 4 on
+  constexpr int NB = LEN >= 4096 ? 2 : 4;
+  constexpr int smem = NB * LEN * (int)sizeof(float2);
+  if (smem > 48 * 1024) {
+    static int attr_dev = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess && attr_dev != dev) {
+      e = cudaFuncSetAttribute(k_fft_cols<LEN, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               smem);
+      if (e == cudaSuccess) attr_dev = dev;
+    }
+    if (e != cudaSuccess) return cuda_check(e, "k_fft_cols attr");
+  }
+  k_fft_cols<LEN, NB><<<p->M1 / NB, kNT, smem, p->stream>>>(z, T, p->M1, p->tw_M2, p->tw4_lo,
+                                                              p->tw4_hi, p->h4);
   return cuda_check(cudaGetLastError(), "k_fft_cols");
 }
 
