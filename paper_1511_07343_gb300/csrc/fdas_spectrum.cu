@@ -51,7 +51,7 @@ template <int LEN, int NB>
 __global__ void __launch_bounds__(kNT) k_fft_rows(const float2* __restrict__ T,
                                                   float2* __restrict__ Zo, int M2,
                                                   const float2* __restrict__ tw_len) {
-  __shared__ float2 buf[NB * LEN];
+  extern __shared__ float2 buf[];  // NB * LEN
   const int tid = threadIdx.x;
   const int b0 = blockIdx.x * NB;
   for (int i = tid; i < NB * LEN; i += kNT) {
@@ -107,8 +107,21 @@ int launch_cols(fdas_plan* p, const float2* z, float2* T) {
 
 template <int LEN>
 int launch_rows(fdas_plan* p, const float2* T, float2* Zo) {
-  constexpr int NB = LEN >= 4096 ? 1 : (LEN >= 2048 ? 2 : 4);
-  k_fft_rows<LEN, NB><<<p->M2 / NB, kNT, 0, p->stream>>>(T, Zo, p->M2, p->tw_M1);
+  // NB rows per CTA: the transposed stores write NB consecutive float2
+  constexpr int NB = LEN >= 4096 ? 2 : 4;
+  constexpr int smem = NB * LEN * (int)sizeof(float2);
+  if (smem > 48 * 1024) {
+    static int attr_dev = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess && attr_dev != dev) {
+      e = cudaFuncSetAttribute(k_fft_rows<LEN, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               smem);
+      if (e == cudaSuccess) attr_dev = dev;
+    }
+    if (e != cudaSuccess) return cuda_check(e, "k_fft_rows attr");
+  }
+  k_fft_rows<LEN, NB><<<p->M2 / NB, kNT, smem, p->stream>>>(T, Zo, p->M2, p->tw_M1);
   return cuda_check(cudaGetLastError(), "k_fft_rows");
 }
 
