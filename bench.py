@@ -736,8 +736,8 @@ def main():
 
 def info_kernels_per_trial():
     # real FFT (columns, rows, unpack), whitening, segment FFTs, correlation,
-    # harmonic sum
-    return 7
+    # harmonic-sum screen and exact sums of the flagged pairs
+    return 8
 
 
 if __name__ == "__main__":

@@ -91,7 +91,8 @@ void free_plan(fdas_plan* p) {
   if (p->count2) cudaFree(p->count2);
   void* ptrs[] = {p->tw_L, p->tw_M1, p->tw_M2, p->tw4_lo, p->tw4_hi, p->twN_lo, p->twN_hi,
                   p->taps, p->bank, p->series, p->zbuf, p->spec, p->spec2, p->white, p->seg,
-                  p->plane, p->q4, p->cands, p->count, p->gbank, p->gstatus,
+                  p->plane, p->q4, p->cands, p->count, p->hs_list, p->hs_nlist,
+                  p->gbank, p->gstatus,
                   p->dkeys, p->dvals, p->taps_ib, p->bank_ib};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -388,6 +389,8 @@ int fdas_plan_create(fdas_plan** out, int64_t N, int32_t zmax, int32_t dz, int32
   p->plane_cap = (int64_t)p->Z * p->nb;
   TRY(dalloc(p, &p->cands, (size_t)max_cands));
   TRY(dalloc(p, &p->count, 1));
+  TRY(dalloc(p, &p->hs_list, (size_t)fdas::kHsListCap));
+  TRY(dalloc(p, &p->hs_nlist, 1));
 
   cudaStream_t s = p->stream;
   TRY(launch_twiddles(p->tw_L, L, 1, L, s));

@@ -8,9 +8,9 @@
 // and (r, j, h, H_h) is a candidate when H_h >= T_h, with T_h the Gamma(h, 1)
 // tail point equal to the Gaussian tail at sigma. All indices are integer
 // arithmetic; the fraction k/h is evaluated as q/16 with q = 16 k / h, so the
-// 16 distinct terms q = 1..16 serve every level:
-//     H_1 = t16, H_2 = H_1 + t8, H_4 = H_2 + (t4 + t12),
-//     H_8 = H_4 + ((t2 + t6) + (t10 + t14)), H_16 = H_8 + (odd q terms).
+// 16 distinct terms q = 1..16 serve every level: with t_q the term of
+// fraction q/16, H_1 = t16, H_2 = t16 + t8, H_4 adds t4 and t12, H_8 adds
+// t2, t6, t10, t14 and H_16 the odd q, one term at a time in that order.
 #include "fdas_common.cuh"
 #include "fdas_emit.cuh"
 #include "fdas_internal.h"
@@ -47,49 +47,48 @@ __global__ void __launch_bounds__(256) k_pool4(const float* __restrict__ P, floa
 // Harmonic sums h >= 2, screened, in a fixed summation order: the fractions
 // q/16 are added one after the other as q = 16, 8 | 4, 12 | 2, 6, 10, 14 |
 // 1, 3, .., 15, so H_2, H_4, H_8 and H_16 are the running sums after 2, 4, 8
-// and 16 terms. A block takes top row j and 16384 consecutive top bins;
+// and 16 terms. A block takes top row j and NT * 64 consecutive top bins;
 // warp w takes the 2048 bins from R0w = R0 + 2048 w and lane l the 64 bins
-// R0w + 64 l + i. For fraction q the sub-harmonic bin is
+// R0w + 64 l + i, as 32 pairs of 2 bins. For fraction q the sub-harmonic bin
+// is
 //     rr = round(q r / 16) = q R0w/16 + 4 q l + K(q, i),  K(q, i) = (2 q i + 16) >> 5,
 // so its 4-bin group, relative to the warp's first, is q l + (K(q, i) >> 2):
-// a compile-time offset from q l. Each warp stages its own slice of row
-// jz(q) of Q4 (32 q + 1 groups) in shared memory, split into 2^a classes by
-// index mod 2^a (q = 2^a b, b odd): lanes then read at stride b, which is
-// odd, so reads are free of bank conflicts; copies are coalesced cp.async
-// (16-byte for odd q, whose slice is contiguous), two fractions ahead, and
-// warps never wait for one another. Each term is bounded by its group
-// maximum, each pair of adjacent bins shares one bound (the larger of its
-// groups); float addition is monotone, so a pair whose running bound stays
-// below T_h cannot hold a candidate at level h. The rare flagged pairs are
-// summed exactly from P in the same order and compared with T_h.
+// lane l needs the groups q l .. q l + omax(q) (omax <= q), a compile-time
+// offset from q l for every pair. Each warp copies its slice of row jz(q) of
+// Q4 (32 q + 1 groups at most) into shared memory with 16-byte cp.async, two
+// fractions ahead, and every lane reads its own groups as one vector per 4
+// (q = 0 mod 4, 16-byte chunks XOR-swizzled within rows of 8 so that a
+// quarter-warp hits 8 bank groups), per 2 (q = 2 mod 4, odd 8-byte stride) or
+// one by one (odd q, odd stride); the group just past a lane's range is the
+// next lane's first (a shuffle). Each pair's term is bounded by the maximum
+// of the (one or two) groups its two sub-harmonic bins fall in; float
+// addition is monotone, so a pair whose running bound stays below T_h holds
+// no candidate at level h. The rare flagged pairs are summed exactly from P
+// in the same order and compared with T_h.
 __host__ __device__ constexpr int frac_order(int i) {
   return i == 0 ? 16 : i == 1 ? 8 : i == 2 ? 4 : i == 3 ? 12 : i < 8 ? 2 + 4 * (i - 4)
                                                                      : 1 + 2 * (i - 8);
 }
 __host__ __device__ constexpr int kq(int q, int i) { return (2 * q * i + 16) >> 5; }
-__host__ __device__ constexpr int ctz5(int q) {
-  return (q & 1) ? 0 : (q & 2) ? 1 : (q & 4) ? 2 : (q & 8) ? 3 : 4;
-}
-// words between classes (a >= 1): >= 32 b + 1 entries and = 32 >> a mod 32,
-// so the 2^a classes of one copy round start on distinct banks
-__host__ __device__ constexpr int class_stride(int q) {
-  return 32 * (q >> ctz5(q)) + (32 >> ctz5(q));
-}
 
-// a block is NT threads (128 or 256: the harmonic-sum tiling the batch
-// autotuner chooses), each warp independent of the others
-constexpr int kHsCells = 64;
-constexpr int kWarpSpan = 32 * kHsCells;
-constexpr int kStageW = 16 * 34;  // largest staged slice per warp (q = 16), floats
+constexpr int kHsCells = 64;                  // top bins per lane
+constexpr int kHsPairs = kHsCells / 2;        // bin pairs per lane
+constexpr int kWarpSpan = 32 * kHsCells;      // top bins per warp
+// last group offset a lane reads for fraction q, groups staged per warp
+__host__ __device__ constexpr int omax(int q) { return kq(q, kHsCells - 1) >> 2; }
+__host__ __device__ constexpr int nchunk(int q) {
+  return (32 * q + (omax(q) == q ? 1 : 0) + 3) / 4;
+}
+// 16-byte slot of chunk C of fraction q's slice: for q = 8 and 16, lane l
+// reads chunks (q/4) l + c, and XOR-ing the slot within its row of 8 with
+// (row mod q/4) puts the 8 lanes of a quarter-warp on 8 different bank groups
+__host__ __device__ constexpr int swz(int q, int C) {
+  return (q == 8 || q == 16) ? (C ^ ((C >> 3) & (q / 4 - 1))) : C;
+}
+constexpr int kStageW = 4 * nchunk(16);  // largest staged slice per warp, floats
 template <int NT>
 constexpr size_t hs_smem() { return (size_t)3 * kStageW * (NT / 32) * sizeof(float); }
 
-__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src),
-               "r"(ok ? 4 : 0)
-               : "memory");
-}
 __device__ __forceinline__ void cp_async16(float* dst, const float* src, bool ok) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
@@ -111,73 +110,96 @@ struct HsCtx {
 };
 
 // copy of the warp's slice of row jz(q) of Q4 (fraction number OI in
-// summation order) into rotating buffer OI % 3
+// summation order) into rotating buffer OI % 3; the slice starts at group
+// q R0w / 64, a multiple of 32, and rows hold a multiple of 4 groups, so
+// every 16-byte chunk is aligned and lies entirely inside or outside the row
 template <int OI, int NQ>
 FDAS_DEV void hs_issue(const HsCtx& x) {
   if constexpr (OI < NQ) {
     constexpr int q = frac_order(OI);
-    constexpr int a = ctz5(q), m = (1 << a) - 1;
+    constexpr int NC = nchunk(q);
     float* buf = x.stage + (OI % 3) * kStageW;
     const int row = x.zc + x.sg * ((2 * q * x.ajc + 16) >> 5);
     const int64_t e_lo = (int64_t)q * (x.R0w >> 6);
     const float* src = x.Q4 + (size_t)row * x.nq + e_lo;
-    const int64_t lim = x.nq - e_lo;  // entries e < lim exist
-    if constexpr (a == 0) {
-      // contiguous slice of 32 q + 1 entries: 16-byte chunks (nq is a
-      // multiple of 4, so a chunk is entirely inside or outside the row)
-      constexpr int nchunk = (32 * q + 1 + 3) / 4;
+    const int64_t lim = x.nq - e_lo;  // groups e < lim exist
 #pragma unroll
-      for (int c0 = 0; c0 < nchunk; c0 += 32) {
-        const int c = c0 + x.lane;
-        if (c0 + 32 <= nchunk || c < nchunk) cp_async16(buf + 4 * c, src + 4 * c, 4 * c < lim);
-      }
-    } else {
-      constexpr int CS = class_stride(q);
-      float* sb = buf + (x.lane & m) * CS + (x.lane >> a);
-      const float* sl = src + x.lane;
-      const int64_t llim = lim - x.lane;
-#pragma unroll
-      for (int k = 0; k < q; ++k) cp_async4(sb + k * (32 >> a), sl + 32 * k, 32 * k < llim);
-      if (x.lane == 0) cp_async4(sb + q * (32 >> a), sl + 32 * q, 32 * q < llim);
+    for (int c0 = 0; c0 < NC; c0 += 32) {
+      const int C = c0 + x.lane;
+      if (c0 + 32 <= NC || C < NC) cp_async16(buf + 4 * swz(q, C), src + 4 * C, 4 * C < lim);
     }
   }
   cp_async_commit();
 }
 
+// the groups q l .. q l + omax(q) of this lane, from the staged slice
+template <int q>
+FDAS_DEV void hs_groups(const float* buf, int lane, float (&v)[omax(q) + 1]) {
+  constexpr int OM = omax(q);
+  if constexpr (q % 4 == 0) {
+    constexpr int k = q / 4;
+    const float4* b4 = reinterpret_cast<const float4*>(buf);
+#pragma unroll
+    for (int c = 0; c < k; ++c) {
+      const float4 t = b4[swz(q, k * lane + c)];
+      v[4 * c] = t.x;
+      v[4 * c + 1] = t.y;
+      v[4 * c + 2] = t.z;
+      if (4 * c + 3 <= OM) v[4 * c + 3] = t.w;
+    }
+  } else if constexpr (q % 2 == 0) {
+    constexpr int k = q / 2;
+    const float2* b2 = reinterpret_cast<const float2*>(buf);
+#pragma unroll
+    for (int c = 0; c < k; ++c) {
+      const float2 t = b2[k * lane + c];
+      v[2 * c] = t.x;
+      if (2 * c + 1 <= OM) v[2 * c + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int o = 0; o <= OM; ++o) v[o] = buf[q * lane + o];
+  }
+  if constexpr (q % 2 == 0 && OM == q) {
+    // group q (l + 1) is the next lane's first; lane 31 reads it (chunk 8 q,
+    // which no swizzle moves)
+    const float nx = __shfl_down_sync(0xffffffffu, v[0], 1);
+    v[q] = lane == 31 ? buf[32 * q] : nx;
+  }
+}
+
 template <int OI, int NQ>
-FDAS_DEV void hs_steps(const HsCtx& x, float2 (&acc)[kHsCells / 4], unsigned& pmask,
+FDAS_DEV void hs_steps(const HsCtx& x, float2 (&acc)[kHsPairs / 2], unsigned& pmask,
                        const Thr& thr) {
   if constexpr (OI < NQ) {
     constexpr int q = frac_order(OI);
-    constexpr int a = ctz5(q), m = (1 << a) - 1, b = q >> a;
-    constexpr int CS = a == 0 ? 0 : class_stride(q);
     cp_async_wait1();
     __syncwarp();
     hs_issue<OI + 2, NQ>(x);
-    const float* sb = x.stage + (OI % 3) * kStageW + b * x.lane;
+    float v[omax(q) + 1];
+    hs_groups<q>(x.stage + (OI % 3) * kStageW, x.lane, v);
 #pragma unroll
-    for (int pp = 0; pp < kHsCells / 4; ++pp) {
-      float v[2];
+    for (int pp = 0; pp < kHsPairs / 2; ++pp) {
+      float b[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int pr = 2 * pp + h;
-        const int o1 = kq(q, 2 * pr) >> 2;
-        const int o2 = kq(q, 2 * pr + 1) >> 2;
-        v[h] = sb[(o1 & m) * CS + (o1 >> a)];
-        if (o2 != o1) v[h] = fmaxf(v[h], sb[(o2 & m) * CS + (o2 >> a)]);
+        const int i = 2 * pp + h;
+        const int o1 = kq(q, 2 * i) >> 2;
+        const int o2 = kq(q, 2 * i + 1) >> 2;  // o1 or o1 + 1
+        b[h] = o2 == o1 ? v[o1] : fmaxf(v[o1], v[o2]);
       }
-      const float2 v2 = make_float2(v[0], v[1]);
-      acc[pp] = (OI == 0) ? v2 : __fadd2_rn(acc[pp], v2);
+      const float2 b2 = make_float2(b[0], b[1]);
+      acc[pp] = (OI == 0) ? b2 : __fadd2_rn(acc[pp], b2);
     }
     if constexpr (OI == 1 || OI == 3 || OI == 7 || OI == 15) {
       constexpr int lvl = OI == 1 ? 1 : (OI == 3 ? 2 : (OI == 7 ? 3 : 4));
       const float t = thr.t[lvl];
       float mx = fmaxf(acc[0].x, acc[0].y);
 #pragma unroll
-      for (int pp = 1; pp < kHsCells / 4; ++pp) mx = fmaxf(mx, fmaxf(acc[pp].x, acc[pp].y));
+      for (int pp = 1; pp < kHsPairs / 2; ++pp) mx = fmaxf(mx, fmaxf(acc[pp].x, acc[pp].y));
       if (mx >= t) {
 #pragma unroll
-        for (int pp = 0; pp < kHsCells / 4; ++pp) {
+        for (int pp = 0; pp < kHsPairs / 2; ++pp) {
           if (acc[pp].x >= t) pmask |= 1u << (2 * pp);
           if (acc[pp].y >= t) pmask |= 1u << (2 * pp + 1);
         }
@@ -189,9 +211,51 @@ FDAS_DEV void hs_steps(const HsCtx& x, float2 (&acc)[kHsCells / 4], unsigned& pm
   }
 }
 
+// Exact H_h of top bins r and r + 1 of row j, in the order of the screen,
+// and the candidates among them (r >= 1, r + 1 < nb). The 2 x NQ loads are
+// independent and issued together.
+template <int NQ>
+FDAS_DEV void hs_exact_pair(const float* __restrict__ P, int64_t nb, int j, int zc, int r,
+                            const Thr& thr, fdas_cand* __restrict__ out,
+                            unsigned long long* count, int64_t maxc) {
+  const int jc = j - zc;
+  const int ajc = jc < 0 ? -jc : jc, sg = jc < 0 ? -1 : 1;
+  float H[2] = {0.f, 0.f};
+#pragma unroll
+  for (int oi = 0; oi < NQ; ++oi) {
+    const int q = frac_order(oi);
+    const float* row = P + (size_t)(zc + sg * ((2 * q * ajc + 16) >> 5)) * nb;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float v = __ldg(row + ((2 * q * (r + c) + 16) >> 5));
+      H[c] = (oi == 0) ? v : H[c] + v;
+    }
+    if (oi == 1 || oi == 3 || oi == 7 || oi == 15) {
+      const int lvl = oi == 1 ? 1 : (oi == 3 ? 2 : (oi == 7 ? 3 : 4));
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (r + c >= 1 && H[c] >= thr.t[lvl]) {
+          const unsigned long long slot = atomicAdd(count, 1ull);
+          if (slot < (unsigned long long)maxc) {
+            fdas_cand cd;
+            cd.r_top = r + c;
+            cd.z_idx = j;
+            cd.h = 1 << lvl;
+            cd.power = H[c];
+            out[slot] = cd;
+          }
+        }
+      }
+    }
+  }
+}
+
+// The screen. Flagged pairs go to a list, (j << 32) | r, for k_harmsum_exact;
+// a lane whose flags do not fit the list (capacity cap) sums them itself.
 template <int NLEV, int NT>
 __global__ void __launch_bounds__(NT) k_harmsum_staged(
     const float* __restrict__ P, const float* __restrict__ Q4, int64_t nb, int Z, Thr thr,
+    unsigned long long* __restrict__ list, unsigned int* nlist, int64_t cap,
     fdas_cand* __restrict__ out, unsigned long long* count, int64_t maxc) {
   constexpr int NQ = 1 << (NLEV - 1);
   extern __shared__ __align__(16) float stage[];  // per warp: 3 rotating buffers
@@ -207,47 +271,40 @@ __global__ void __launch_bounds__(NT) k_harmsum_staged(
   const int jc = j - x.zc;
   x.ajc = jc < 0 ? -jc : jc;
   x.sg = jc < 0 ? -1 : 1;
-  const int zc = x.zc, sg = x.sg, ajc = x.ajc;
-  float2 acc[kHsCells / 4];
+  float2 acc[kHsPairs / 2];
   unsigned pmask = 0;
   hs_issue<0, NQ>(x);
   hs_issue<1, NQ>(x);
   hs_steps<0, NQ>(x, acc, pmask, thr);
-  // pairs past the end of the spectrum
+  // pairs past the end of the spectrum (nb - first is even)
   const int64_t first = x.R0w + (int64_t)kHsCells * x.lane;
   if (first >= nb) pmask = 0;
   else if (first + kHsCells > nb) pmask &= (1u << ((nb - first) >> 1)) - 1u;
-  // exact sums of the flagged pairs, same order as the bound
-  while (pmask) {
-    const int pr = __ffs(pmask) - 1;
+  if (pmask == 0) return;
+  const unsigned n = (unsigned)__popc(pmask);
+  const unsigned long long base = atomicAdd(nlist, n);
+  const unsigned long long key = (unsigned long long)j << 32;
+  for (unsigned k = 0; pmask; ++k) {
+    const int r = (int)(first + 2 * (__ffs(pmask) - 1));
     pmask &= pmask - 1;
-    for (int c = 0; c < 2; ++c) {
-      const int64_t r64 = first + 2 * pr + c;
-      if (r64 < 1 || r64 >= nb) continue;
-      const int r = (int)r64;
-      float H = 0.f;
-#pragma unroll
-      for (int oi = 0; oi < NQ; ++oi) {
-        const int q = frac_order(oi);
-        const int jzq = zc + sg * ((2 * q * ajc + 16) >> 5);
-        const float v = __ldg(P + (size_t)jzq * nb + ((2 * q * r + 16) >> 5));
-        H = (oi == 0) ? v : H + v;
-        if (oi == 1 || oi == 3 || oi == 7 || oi == 15) {
-          const int lvl = oi == 1 ? 1 : (oi == 3 ? 2 : (oi == 7 ? 3 : 4));
-          if (H >= thr.t[lvl]) {
-            const unsigned long long slot = atomicAdd(count, 1ull);
-            if (slot < (unsigned long long)maxc) {
-              fdas_cand cd;
-              cd.r_top = r;
-              cd.z_idx = j;
-              cd.h = 1 << lvl;
-              cd.power = H;
-              out[slot] = cd;
-            }
-          }
-        }
-      }
-    }
+    if (base + k < (unsigned long long)cap) list[base + k] = key | (unsigned)r;
+    else hs_exact_pair<NQ>(P, nb, j, x.zc, r, thr, out, count, maxc);
+  }
+}
+
+// Exact sums of the listed pairs (grid-stride over the list).
+template <int NLEV>
+__global__ void __launch_bounds__(256) k_harmsum_exact(
+    const float* __restrict__ P, const unsigned long long* __restrict__ list,
+    const unsigned int* nlist, int64_t cap, int64_t nb, int Z, Thr thr,
+    fdas_cand* __restrict__ out, unsigned long long* count, int64_t maxc) {
+  constexpr int NQ = 1 << (NLEV - 1);
+  const int64_t n = min((int64_t)*nlist, cap);
+  const int zc = (Z - 1) / 2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long e = list[i];
+    hs_exact_pair<NQ>(P, nb, (int)(e >> 32), zc, (int)(e & 0xffffffffu), thr, out, count, maxc);
   }
 }
 
@@ -284,11 +341,22 @@ int hs_launch(fdas_plan* p, const float* d_plane, const float* d_q4, fdas_cand* 
     if (e != cudaSuccess) return cuda_check(e, "k_harmsum_staged attr");
     attr_dev = dev;
   }
+  e = cudaMemsetAsync(p->hs_nlist, 0, sizeof(unsigned int), p->stream);
+  if (e != cudaSuccess) return cuda_check(e, "memset flagged-pair count");
   const int64_t w = plane_width(p);
   dim3 grid((unsigned)((w + NT * kHsCells - 1) / (NT * kHsCells)), p->Z);
   k_harmsum_staged<NLEV, NT><<<grid, NT, hs_smem<NT>(), p->stream>>>(
-      d_plane, d_q4, w, p->Z, thresholds_of(p), d_out, d_count, p->max_cands);
-  return cuda_check(cudaGetLastError(), "k_harmsum_staged");
+      d_plane, d_q4, w, p->Z, thresholds_of(p), p->hs_list, p->hs_nlist, kHsListCap, d_out,
+      d_count, p->max_cands);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(e, "k_harmsum_staged");
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_check(e, "SM count");
+  k_harmsum_exact<NLEV><<<4 * sms, 256, 0, p->stream>>>(d_plane, p->hs_list, p->hs_nlist,
+                                                        kHsListCap, w, p->Z, thresholds_of(p),
+                                                        d_out, d_count, p->max_cands);
+  return cuda_check(cudaGetLastError(), "k_harmsum_exact");
 }
 
 template <int NT>

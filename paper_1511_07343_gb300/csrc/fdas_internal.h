@@ -45,6 +45,10 @@ struct fdas_plan {
   float* q4 = nullptr;         // Z x nb/4 maxima of 4 consecutive plane bins
   fdas_cand* cands = nullptr;  // max_cands
   unsigned long long* count = nullptr;
+  // pairs of top bins the harmonic-sum screen flags, (j << 32) | r, for the
+  // exact sums (kHsListCap entries; flags past the capacity are summed inline)
+  unsigned long long* hs_list = nullptr;
+  unsigned int* hs_nlist = nullptr;
 
   // tensor-core correlation (precision variant); corr_mode = FDAS_CORR_*
   int corr_mode = 0;
@@ -78,6 +82,9 @@ struct fdas_plan {
 };
 
 namespace fdas {
+
+// capacity of the harmonic-sum screen's list of flagged bin pairs
+constexpr int64_t kHsListCap = (int64_t)1 << 20;
 
 // plane columns: nb, or 2 nb (half bins) for half-bin planes
 inline int64_t plane_width(const fdas_plan* p) { return p->nb << p->interbin; }

@@ -37,13 +37,14 @@ DEFAULT_CLASSES = {50: (128, 2048), 100: (256, 4096), 200: (512, 8192)}
 def plan_footprint(n_max: int, zmax: int, m: int, L: int, dz: int = 2,
                    max_cands: int = 1 << 20) -> int:
     """Device bytes a plan of this class holds, for admission: plane and its
-    4-bin maxima, spectra and workspaces, segment spectra, templates and the
-    candidate list (an upper estimate of fdas_plan_get_info's device_bytes)."""
+    4-bin maxima, spectra and workspaces, segment spectra, templates, the
+    candidate list and the harmonic-sum screen's list of 2^20 flagged pairs
+    (an upper estimate of fdas_plan_get_info's device_bytes)."""
     Z = 2 * (zmax // dz) + 1
     nb = n_max // 2
     S = (nb + (L - m) - 1) // (L - m)
     core = (4 * Z * nb + Z * nb + 8 * 4 * nb + 8 * S * L + 24 * Z * L
-            + 16 * max_cands + 4 * n_max)
+            + 16 * max_cands + 4 * n_max + 8 * (1 << 20))
     # twiddle tables and counters (a few MB at most), plus 2% headroom
     return int(core * 1.02) + (8 << 20)
 

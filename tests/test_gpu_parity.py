@@ -179,6 +179,38 @@ def test_harmonic_sum_on_integer_plane_is_exact(gpu_lib):
         assert got[(c[0], c[1], c[2])] == c[3]
 
 
+def test_harmonic_sum_with_more_flags_than_the_list_holds(gpu_lib):
+    """A plane of powers 3..5 flags every bin pair at h = 16 (1.34 million
+    pairs, more than the screen's list of 2^20 entries), so the list kernel
+    sums the first 2^20 and the screen the rest inline; integer powers keep
+    every float32 sum exact, so the lists must be equal."""
+    fd = gpu_lib
+    N, zmax, dz = 1 << 17, 40, 2
+    Z, nb = 41, N // 2
+    rng = np.random.default_rng(10)
+    P = rng.integers(3, 6, size=(Z, nb)).astype(np.float64)
+    plan = make_plan(fd, N, zmax, dz, 64, 2048, 16, max_cands=1 << 23)
+    try:
+        info = fd.fdas_plan_get_info(plan)
+        d_p = torch.from_numpy(P.astype(np.float32).ravel()).to(DEV)
+        d_out = torch.empty(info.max_cands * 4, dtype=torch.int32, device=DEV)
+        d_cnt = torch.zeros(1, dtype=torch.int64, device=DEV)
+        fd.fdas_stage_harmsum(plan, d_p, d_out, d_cnt)
+        torch.cuda.synchronize()
+    finally:
+        fd.fdas_plan_destroy(plan)
+    n = int(d_cnt.item())
+    arr = d_out.cpu().numpy().view(fd.CAND_DTYPE)[:n]
+    cands, _ = O.candidates(P, 16, 6.0)
+    assert n == len(cands) > (1 << 21)
+    got = np.sort(arr[["h", "r_top", "z_idx"]].astype([("h", "<i4"), ("r_top", "<i4"),
+                                                       ("z_idx", "<i4")]), order=["h", "r_top", "z_idx"])
+    want = np.array([(c[2], c[0], c[1]) for c in cands],
+                    dtype=[("h", "<i4"), ("r_top", "<i4"), ("z_idx", "<i4")])
+    want.sort(order=["h", "r_top", "z_idx"])
+    assert np.array_equal(got, want)
+
+
 # --------------------------------------------------------------- full path --
 def test_search_cfg1_matches_oracle(gpu_lib):
     fd = gpu_lib
