@@ -121,12 +121,21 @@ FDAS_DEV void hs_issue(const HsCtx& x) {
     float* buf = x.stage + (OI % 3) * kStageW;
     const int row = x.zc + x.sg * ((2 * q * x.ajc + 16) >> 5);
     const int64_t e_lo = (int64_t)q * (x.R0w >> 6);
-    const float* src = x.Q4 + (size_t)row * x.nq + e_lo;
-    const int64_t lim = x.nq - e_lo;  // groups e < lim exist
+    // per lane: chunks C = lane + 32 i; the swizzle of chunk C depends on
+    // lane only (32 i keeps the row's low bits), so the addresses are a
+    // lane base plus compile-time offsets
+    const float* src = x.Q4 + (size_t)row * x.nq + e_lo + 4 * x.lane;
+    float* dst = buf + 4 * swz(q, x.lane);
+    constexpr int full = NC / 32, rest = NC % 32;
+    if (e_lo + 4 * NC <= x.nq) {  // the whole slice lies inside the row
 #pragma unroll
-    for (int c0 = 0; c0 < NC; c0 += 32) {
-      const int C = c0 + x.lane;
-      if (c0 + 32 <= NC || C < NC) cp_async16(buf + 4 * swz(q, C), src + 4 * C, 4 * C < lim);
+      for (int i = 0; i < full; ++i) cp_async16(dst + 128 * i, src + 128 * i, true);
+      if (rest && x.lane < rest) cp_async16(dst + 128 * full, src + 128 * full, true);
+    } else {
+      const int64_t lim = x.nq - e_lo - 4 * x.lane;  // this lane's chunk i exists if 128 i < lim
+#pragma unroll
+      for (int i = 0; i < full; ++i) cp_async16(dst + 128 * i, src + 128 * i, 128 * i < lim);
+      if (rest && x.lane < rest) cp_async16(dst + 128 * full, src + 128 * full, 128 * full < lim);
     }
   }
   cp_async_commit();

@@ -156,20 +156,27 @@ int dispatch_rows(fdas_plan* p, const float2* T, float2* Zo) {
 // ----------------------------------------------------------------------------
 // Whitening: mu_k = even-count median of |X|^2 over the 64-bin window of bin
 // k ([k-32, k+31] shifted into [1, nb-1]); Xw_k = X_k sqrt(ln2 / mu_k).
-// A CTA takes 64 consecutive bins: the union of their windows (<= 127
-// powers) is sorted once in shared memory as 32-bit keys - the power's bit
-// pattern (powers are >= 0, so bit patterns order like values) with its low
-// 7 mantissa bits replaced by the entry's index - and the medians read the
-// exact powers back by index. (Two powers within 2^-16 of each other may
-// swap places in that order, which moves a median by less than 2^-16
-// relative.) For each run of 32 sorted entries a 128-bit mask records which
-// indices it holds; a warp skips the runs below its lanes' 32nd in-window
-// entries by popcount and then walks the sorted list in step, every lane
-// reading the same entry.
+// One warp takes 64 consecutive bins (a tile); no CTA barrier is used.
+//  1. The union of the tile's windows (at most 127 bins from u0) is loaded
+//     as 128 exact 64-bit keys (power bits, entry index; powers are >= 0, so
+//     their bit patterns order like their values, and entries past the
+//     spectrum get the largest keys) and sorted by a bitonic network in
+//     registers: slot i = 4 lane + w, compare-exchanges at distance 1 and 2
+//     inside a lane, at distance >= 4 through shuffles.
+//  2. pos[e] = sorted slot of entry e. The window of offset o (entries
+//     o .. o+63) is the 128-bit mask M(o) of the slots its entries hold:
+//     M(0) is an XOR reduction of the bits of entries 0..63 over the warp,
+//     and M(o) = M(0) ^ XOR_{i<o} (bit(pos[i]) ^ bit(pos[i+64])), an
+//     exclusive XOR scan over the lanes; lane l gets M(2l) and M(2l+1).
+//  3. Bin k = k0 + 2l + c has offset wstart(k) - u0 (= 2l + c unless a
+//     window of the tile is shifted at a spectrum edge; then its mask comes
+//     from the lane holding it); its median is
+//     the mean of the sorted powers at the 32nd and 33rd set bits of its mask.
 // ----------------------------------------------------------------------------
 constexpr int kWin = 64;
-constexpr int kWTile = 64;
-constexpr int kSortN = 128;
+constexpr int kWTile = 64;       // bins per warp
+constexpr int kSortN = 128;      // sorted entries per warp
+constexpr int kWWarps = 8;       // warps (tiles) per CTA
 
 __device__ __forceinline__ int64_t wstart(int64_t k, int64_t nb) {
   int64_t s = k - kWin / 2;
@@ -177,84 +184,153 @@ __device__ __forceinline__ int64_t wstart(int64_t k, int64_t nb) {
   return s > nb - kWin ? nb - kWin : s;
 }
 
-__global__ void __launch_bounds__(kWTile) k_whiten(const float2* __restrict__ X,
-                                                   float2* __restrict__ Xw, int64_t nb) {
-  __shared__ unsigned skey[kSortN];
-  __shared__ float spow[kSortN];
-  __shared__ unsigned long long cmask[kSortN / 32][2];
-  const int tid = threadIdx.x;
-  if (tid < kSortN / 16) cmask[tid >> 1][tid & 1] = 0ull;
-  const int64_t k0 = (int64_t)blockIdx.x * kWTile;
-  const int64_t klast = (k0 + kWTile - 1 < nb - 1) ? k0 + kWTile - 1 : nb - 1;
-  const int64_t lo = wstart(k0 < 1 ? 1 : k0, nb);
-  const int64_t hi = wstart(klast, nb) + kWin - 1;
-  const int cnt = (int)(hi - lo + 1);
-  for (int t = tid; t < kSortN; t += kWTile) {
-    unsigned key = ~0u;
-    if (t < cnt) {
-      const float pw = cnorm(X[lo + t]);
-      spow[t] = pw;
-      key = (__float_as_uint(pw) & ~0x7Fu) | (unsigned)t;
-    }
-    skey[t] = key;
+struct Bits128 {
+  unsigned long long lo, hi;
+};
+FDAS_DEV Bits128 bit128(unsigned p) {
+  const unsigned long long b = 1ull << (p & 63u);
+  return Bits128{p < 64 ? b : 0ull, p < 64 ? 0ull : b};
+}
+FDAS_DEV Bits128 operator^(Bits128 a, Bits128 b) { return Bits128{a.lo ^ b.lo, a.hi ^ b.hi}; }
+FDAS_DEV Bits128 shfl128(Bits128 a, int src) {
+  return Bits128{__shfl_sync(0xffffffffu, a.lo, src), __shfl_sync(0xffffffffu, a.hi, src)};
+}
+
+// position of the set bit of rank r (0-based) of m (m has more than r set bits)
+FDAS_DEV int select128(Bits128 m, int r) {
+  const int c = __popcll(m.lo);
+  const unsigned long long x = r < c ? m.lo : m.hi;
+  int base = r < c ? 0 : 64;
+  r = r < c ? r : r - c;
+  unsigned w = (unsigned)x;
+  const int c32 = __popc(w);
+  if (r >= c32) {
+    w = (unsigned)(x >> 32);
+    base += 32;
+    r -= c32;
   }
-  __syncthreads();
-  // bitonic sort, ascending, one compare-exchange per thread per step
+#pragma unroll
+  for (int sh = 16; sh >= 1; sh >>= 1) {
+    const int cs = __popc(w & ((1u << sh) - 1u));
+    if (r >= cs) {
+      r -= cs;
+      w >>= sh;
+      base += sh;
+    }
+  }
+  return base;
+}
+
+__global__ void __launch_bounds__(32 * kWWarps) k_whiten(const float2* __restrict__ X,
+                                                         float2* __restrict__ Xw, int64_t nb) {
+  __shared__ __align__(16) float sval[kWWarps][kSortN];
+  __shared__ __align__(4) unsigned char spos[kWWarps][kSortN];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t k0 = ((int64_t)blockIdx.x * kWWarps + warp) * kWTile;
+  if (k0 >= nb) return;  // the whole warp
+  const int64_t u0 = wstart(k0 < 1 ? 1 : k0, nb);
+  // 1. keys; slot 4 lane + w starts with entry lane + 32 w (coalesced loads)
+  unsigned kh[4], kl[4];
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    const int e = lane + 32 * w;
+    const int64_t b = u0 + e;
+    kh[w] = b < nb ? __float_as_uint(cnorm(X[b])) : 0xffffffffu;
+    kl[w] = (unsigned)e;
+  }
+#pragma unroll
   for (int size = 2; size <= kSortN; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      const int a = 2 * stride * (tid / stride) + (tid % stride);
-      const int b = a + stride;
-      const bool up = (a & size) == 0;
-      const unsigned ka = skey[a], kb = skey[b];
-      if ((ka > kb) == up) {
-        skey[a] = kb;
-        skey[b] = ka;
+#pragma unroll
+    for (int d = size >> 1; d >= 1; d >>= 1) {
+      if (d >= 4) {
+        const int ld = d >> 2;
+        // slots 4 lane + w, w < 4: the bits tested here (>= 4) are lane bits
+        const bool asc = ((4 * lane) & size) == 0;
+        const bool keep_min = ((lane & ld) == 0) == asc;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const unsigned oh = __shfl_xor_sync(0xffffffffu, kh[w], ld);
+          const unsigned ol = __shfl_xor_sync(0xffffffffu, kl[w], ld);
+          const bool other_less = oh < kh[w] || (oh == kh[w] && ol < kl[w]);
+          if (other_less == keep_min) {  // keys are distinct (entry index)
+            kh[w] = oh;
+            kl[w] = ol;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          if (w & d) continue;
+          const int v = w | d;
+          const bool asc = ((4 * lane + w) & size) == 0;
+          const bool gt = kh[w] > kh[v] || (kh[w] == kh[v] && kl[w] > kl[v]);
+          if (gt == asc) {
+            const unsigned th = kh[w], tl = kl[w];
+            kh[w] = kh[v];
+            kl[w] = kl[v];
+            kh[v] = th;
+            kl[v] = tl;
+          }
+        }
       }
-      __syncthreads();
     }
   }
-  for (int t = tid; t < cnt; t += kWTile) {
-    const unsigned i = skey[t] & 0x7Fu;
-    atomicOr(&cmask[t >> 5][i >> 6], 1ull << (i & 63));
+  // 2. sorted powers by slot, slot of each entry
+  float* sv = sval[warp];
+  unsigned char* sp = spos[warp];
+  reinterpret_cast<float4*>(sv)[lane] = make_float4(__uint_as_float(kh[0]), __uint_as_float(kh[1]),
+                                                    __uint_as_float(kh[2]), __uint_as_float(kh[3]));
+#pragma unroll
+  for (int w = 0; w < 4; ++w) sp[kl[w]] = (unsigned char)(4 * lane + w);
+  __syncwarp();
+  const unsigned short q01 = reinterpret_cast<const unsigned short*>(sp)[lane];
+  const unsigned short q23 = reinterpret_cast<const unsigned short*>(sp)[lane + 32];
+  const Bits128 b0 = bit128(q01 & 0xffu), b1 = bit128(q01 >> 8);    // entries 2l, 2l+1
+  const Bits128 b2 = bit128(q23 & 0xffu), b3 = bit128(q23 >> 8);    // entries 2l+64, 2l+65
+  Bits128 m0 = b0 ^ b1;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    m0.lo ^= __shfl_xor_sync(0xffffffffu, m0.lo, o);
+    m0.hi ^= __shfl_xor_sync(0xffffffffu, m0.hi, o);
   }
-  __syncthreads();
-  const int64_t k = k0 + tid;
-  const bool live = k < nb;
-  const unsigned s = live ? (unsigned)(wstart(k, nb) - lo) : 0u;  // s <= 63
-  // window bits [s, s + 63] of the 128 relative indices
-  const unsigned long long w0 = ~0ull << s, w1 = s ? (1ull << s) - 1ull : 0ull;
-  int c = 0, t0 = 0;
-  for (; t0 + 32 <= cnt; t0 += 32) {
-    const int n = __popcll(cmask[t0 >> 5][0] & w0) + __popcll(cmask[t0 >> 5][1] & w1);
-    if (c + n >= kWin / 2) break;  // the 32nd in-window entry is in this run
-    c += n;
-  }
-  // walk in step from the warp's lowest start; lanes before their own start
-  // skip entries they have already counted
-  const int tw = __reduce_min_sync(0xffffffffu, t0);
-  int ia = -1, ib = -1;
-  bool done = !live;
-  for (int t = tw; t < cnt && !__all_sync(0xffffffffu, done); ++t) {
-    const unsigned key = skey[t];
-    const unsigned i = key & 0x7Fu;
-    if (!done && t >= t0 && i - s < (unsigned)kWin) {
-      if (c == kWin / 2 - 1) ia = (int)i;
-      if (c == kWin / 2) {
-        ib = (int)i;
-        done = true;
-      }
-      ++c;
+  const Bits128 D0 = b0 ^ b2, dl = D0 ^ (b1 ^ b3);
+  Bits128 inc = dl;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long tlo = __shfl_up_sync(0xffffffffu, inc.lo, o);
+    const unsigned long long thi = __shfl_up_sync(0xffffffffu, inc.hi, o);
+    if (lane >= o) {
+      inc.lo ^= tlo;
+      inc.hi ^= thi;
     }
   }
-  if (!live) return;
-  if (k == 0) {
-    Xw[0] = make_float2(0.f, 0.f);
-    return;
+  Bits128 m[2];
+  m[0] = m0 ^ (inc ^ dl);  // M(2l)
+  m[1] = m[0] ^ D0;        // M(2l+1)
+  // 3. medians and whitened output of bins k0 + 2l, k0 + 2l + 1
+  const int64_t k = k0 + 2 * lane;
+  // a tile with a window shifted at either spectrum edge: offsets differ
+  if (k0 < 1 + kWin / 2 || k0 + (kWTile - 1) - kWin / 2 > nb - kWin) {
+    Bits128 mo[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int off = k + c < nb ? (int)(wstart(k + c, nb) - u0) : 0;  // 0..63
+      const Bits128 a = shfl128(m[0], off >> 1), bb = shfl128(m[1], off >> 1);
+      mo[c] = (off & 1) ? bb : a;
+    }
+    m[0] = mo[0];
+    m[1] = mo[1];
   }
-  const float mu = 0.5f * (spow[ia] + spow[ib]);
-  const float2 x = X[k];
-  const float g = mu > 0.f ? sqrtf(0.69314718055994531f / mu) : 0.f;
-  Xw[k] = make_float2(x.x * g, x.y * g);
+  if (k >= nb) return;  // nb is even: bins k, k + 1 are both in or both out
+  float g[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const float mu = 0.5f * (sv[select128(m[c], kWin / 2 - 1)] + sv[select128(m[c], kWin / 2)]);
+    g[c] = mu > 0.f ? sqrtf(0.69314718055994531f / mu) : 0.f;
+  }
+  if (k == 0) g[0] = 0.f;
+  const float4 x = *reinterpret_cast<const float4*>(X + k);
+  *reinterpret_cast<float4*>(Xw + k) = make_float4(x.x * g[0], x.y * g[0], x.z * g[1], x.w * g[1]);
 }
 
 }  // namespace
@@ -282,8 +358,9 @@ int launch_spectrum(fdas_plan* p, const float* d_series, float2* d_spec) {
 
 int launch_whiten(fdas_plan* p, const float2* d_spec, float2* d_white) {
   if (p->whiten_mode == FDAS_WHITEN_BLOCK) return launch_whiten_block(p, d_spec, d_white);
-  const unsigned nblk = (unsigned)((p->nb + kWTile - 1) / kWTile);
-  k_whiten<<<nblk, kWTile, 0, p->stream>>>(d_spec, d_white, p->nb);
+  const int64_t per_cta = (int64_t)kWTile * kWWarps;
+  const unsigned nblk = (unsigned)((p->nb + per_cta - 1) / per_cta);
+  k_whiten<<<nblk, 32 * kWWarps, 0, p->stream>>>(d_spec, d_white, p->nb);
   return cuda_check(cudaGetLastError(), "k_whiten");
 }
 

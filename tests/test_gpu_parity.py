@@ -117,6 +117,30 @@ def test_spectrum_and_whitening(gpu_lib, logn):
     assert np.max(np.abs(W_gpu - W_orc)) <= 5e-5
 
 
+@pytest.mark.parametrize("N", [1 << 15, 12288])
+def test_whitening_exact_medians_with_ties(gpu_lib, N):
+    """Small-integer spectra make every power exact in float32 and full of
+    ties, so the medians are exact order statistics: the whitened spectrum
+    must match the oracle to float32 rounding of the scale (N = 12288 gives a
+    tile count that is not a multiple of a CTA's tiles)."""
+    fd = gpu_lib
+    nb = N // 2
+    rng = np.random.default_rng(N)
+    X = (rng.integers(1, 4, nb) + 1j * rng.integers(0, 3, nb)).astype(np.complex64)
+    plan = make_plan(fd, N, 20, 2, 64, 2048, 1)
+    try:
+        spec = torch.from_numpy(X.view(np.float32).copy()).to(DEV)
+        white = torch.empty(N, dtype=torch.float32, device=DEV)
+        fd.fdas_stage_whiten(plan, spec, white)
+        torch.cuda.synchronize()
+    finally:
+        fd.fdas_plan_destroy(plan)
+    W_gpu = white.cpu().numpy().view(np.complex64).astype(np.complex128)
+    W_orc = O.whiten(X.astype(np.complex128))
+    assert W_gpu[0] == 0
+    assert np.max(np.abs(W_gpu - W_orc) / np.abs(W_orc[1:]).max()) <= 1e-6
+
+
 # ------------------------------------------------------------------- plane --
 @pytest.mark.parametrize("N,zmax,m,L", [
     (1 << 17, 50, 128, 2048),      # the 2^17-sample workload's shapes
