@@ -275,4 +275,28 @@ FDAS_DEV void dft32_pairs(c2 (&x)[16], float2 (&out)[32]) {
   }
 }
 
+// Radix-32 DFT by decimation in time over index e = 2 p + lane held as 16
+// pairs (p = 0..15, lane 0 = even e, lane 1 = odd e): the two lanes'
+// 16-point DFTs E and O run packed with the same twiddles in both lanes, then
+// outputs k and k + 16 are E[k] +- exp(DIR 2 pi i k / 32) O[k] on scalars.
+// f(n, value) receives output n in natural order; x is overwritten.
+template <int DIR, typename F>
+FDAS_DEV void dft32_dit(c2 (&x)[16], F&& f) {
+  dft2_brev<16, DIR>(x);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const c2 v = x[brev<16>(k)];
+    const float2 E = make_float2(v.re.x, v.im.x);
+    float2 t = make_float2(v.re.y, v.im.y);  // O[k]
+    if (k == 8) {
+      t = DIR > 0 ? make_float2(-t.y, t.x) : make_float2(t.y, -t.x);
+    } else if (k != 0) {
+      const float c = kCos32[k], sn = DIR < 0 ? -kSin32[k] : kSin32[k];
+      t = make_float2(t.x * c - t.y * sn, t.x * sn + t.y * c);
+    }
+    f(k, make_float2(E.x + t.x, E.y + t.y));
+    f(k + 16, make_float2(E.x - t.x, E.y - t.y));
+  }
+}
+
 }  // namespace fdas

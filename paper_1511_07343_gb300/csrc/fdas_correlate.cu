@@ -60,7 +60,8 @@ __host__ __device__ constexpr int pk_ra2() { return L / 512; }
 //        thread (u, a): the pair k1 = 2u, 2u+1, packed
 //   A2 radix-RA2 over a -> Z[k1][c + 16 d], times w_L^{k1 (c + 16 d)}
 //        16/RA2 packed butterflies (u, c) per thread
-//   B  radix-32 over k1 -> c[n2 + NA n1]     thread n2
+//   B  radix-32 over k1 -> c[n2 + NA n1]     thread n2 (two packed radix-16
+//        DFTs of the even and odd k1, then a scalar radix-2 combination)
 // All butterflies work on packed f32x2 pairs (two transforms per FP32
 // instruction). Two shared-memory exchanges per pair and three CTA barriers
 // (A1 -> A2, A2 -> B, and B's reads done before the next pair's A1 writes);
@@ -235,11 +236,8 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
     for (int u = 0; u < 16; ++u) y[u] = c2_of(X[xsw(tid, u)]);
     // every warp has read X: the next pair's A1 may overwrite it
     __syncthreads();
-    float2 out[32];
-    dft32_pairs<kInv>(y, out);
     // every output goes to Ps[n] (room for all L); the valid V start at half_m
-#pragma unroll
-    for (int e = 0; e < 32; ++e) Ps[tid + NA * brev<32>(e)] = cnorm(out[e]);
+    dft32_dit<kInv>(y, [&](int e, float2 o) { Ps[tid + NA * e] = cnorm(o); });
     // Outputs n .. n+3 (n % 4 == 0) come from threads n % NA .. +3, lanes of
     // one warp; so each warp stores the float4s its own lanes produced and a
     // warp barrier suffices (the next pair writes Ps only after its first
