@@ -275,6 +275,21 @@ FDAS_DEV void dft32_pairs(c2 (&x)[16], float2 (&out)[32]) {
   }
 }
 
+// 16-byte asynchronous global -> shared copy (L2 only); with ok false the
+// destination is zero-filled and nothing is read.
+FDAS_DEV void cp_async16(void* dst, const void* src, bool ok = true) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+               "r"(ok ? 16 : 0)
+               : "memory");
+}
+FDAS_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most N of this thread's committed copy groups are pending
+template <int N>
+FDAS_DEV void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Radix-32 DFT by decimation in time over index e = 2 p + lane held as 16
 // pairs (p = 0..15, lane 0 = even e, lane 1 = odd e): the two lanes'
 // 16-point DFTs E and O run packed with the same twiddles in both lanes, then

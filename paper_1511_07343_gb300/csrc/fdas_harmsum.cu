@@ -89,19 +89,6 @@ constexpr int kStageW = 4 * nchunk(16);  // largest staged slice per warp, float
 template <int NT>
 constexpr size_t hs_smem() { return (size_t)3 * kStageW * (NT / 32) * sizeof(float); }
 
-__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool ok) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
-               "r"(ok ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait1() {
-  asm volatile("cp.async.wait_group 1;" ::: "memory");
-}
-
 struct HsCtx {
   float* stage;  // this warp's 3 rotating buffers
   const float* Q4;
@@ -182,7 +169,7 @@ FDAS_DEV void hs_steps(const HsCtx& x, float2 (&acc)[kHsPairs / 2], unsigned& pm
                        const Thr& thr) {
   if constexpr (OI < NQ) {
     constexpr int q = frac_order(OI);
-    cp_async_wait1();
+    cp_async_wait<1>();
     __syncwarp();
     hs_issue<OI + 2, NQ>(x);
     float v[omax(q) + 1];
