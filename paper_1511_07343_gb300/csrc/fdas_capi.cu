@@ -92,7 +92,7 @@ void free_plan(fdas_plan* p) {
   void* ptrs[] = {p->tw_L, p->tw_M1, p->tw_M2, p->tw4_lo, p->tw4_hi, p->twN_lo, p->twN_hi,
                   p->taps, p->bank, p->series, p->zbuf, p->spec, p->spec2, p->white, p->seg,
                   p->plane, p->q4, p->cands, p->count, p->hs_list, p->hs_nlist,
-                  p->gbank, p->gstatus,
+                  p->hs_order[0], p->hs_order[1], p->gbank, p->gstatus,
                   p->dkeys, p->dvals, p->taps_ib, p->bank_ib};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -391,6 +391,7 @@ int fdas_plan_create(fdas_plan** out, int64_t N, int32_t zmax, int32_t dz, int32
   TRY(dalloc(p, &p->count, 1));
   TRY(dalloc(p, &p->hs_list, (size_t)fdas::kHsListCap));
   TRY(dalloc(p, &p->hs_nlist, 1));
+  TRY(make_hs_order(p));
 
   cudaStream_t s = p->stream;
   TRY(launch_twiddles(p->tw_L, L, 1, L, s));
@@ -520,7 +521,7 @@ int fdas_plan_set_interbin(fdas_plan* p, int32_t enable) {
   if (!p) return set_error(FDAS_ERR_INVALID, "NULL plan");
   if (!enable) {
     p->interbin = 0;
-    return FDAS_OK;
+    return make_hs_order(p);
   }
   if (p->corr_mode != FDAS_CORR_FFT)
     return set_error(FDAS_ERR_INVALID, "half-bin planes use the FFT correlation only");
@@ -544,6 +545,7 @@ int fdas_plan_set_interbin(fdas_plan* p, int32_t enable) {
     p->plane_cap = need;
   }
   p->interbin = 1;
+  if ((rc = make_hs_order(p))) return rc;
   return cuda_check(cudaStreamSynchronize(p->stream), "half-bin templates");
 }
 
@@ -683,11 +685,15 @@ int batch_view(fdas_batch* b, int64_t N, fdas_plan** out) {
     }
   fdas_plan* v = new fdas_plan(*base);  // shares the workspaces and templates
   v->tw_M1 = v->tw_M2 = v->tw4_lo = v->tw4_hi = v->twN_lo = v->twN_hi = nullptr;
+  v->hs_order[0] = v->hs_order[1] = nullptr;
+  v->hs_order_w = 0;
   v->device_bytes = 0;
   int rc = set_geometry(v, N);
   if (!rc) rc = alloc_geometry_tables(v);
+  if (!rc) rc = make_hs_order(v);
   if (rc) {
     free_geometry_tables(v);
+    free_hs_order(v);
     delete v;
     return rc;
   }
@@ -837,6 +843,7 @@ int fdas_batch_destroy(fdas_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   for (fdas_plan* v : b->views) {
     free_geometry_tables(v);
+    free_hs_order(v);
     delete v;
   }
   fdas_plan_destroy(b->base);

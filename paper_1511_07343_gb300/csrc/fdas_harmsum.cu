@@ -11,6 +11,10 @@
 // 16 distinct terms q = 1..16 serve every level: with t_q the term of
 // fraction q/16, H_1 = t16, H_2 = t16 + t8, H_4 adds t4 and t12, H_8 adds
 // t2, t6, t10, t14 and H_16 the odd q, one term at a time in that order.
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
 #include "fdas_common.cuh"
 #include "fdas_emit.cuh"
 #include "fdas_internal.h"
@@ -248,20 +252,25 @@ FDAS_DEV void hs_exact_pair(const float* __restrict__ P, int64_t nb, int j, int 
 
 // The screen. Flagged pairs go to a list, (j << 32) | r, for k_harmsum_exact;
 // a lane whose flags do not fit the list (capacity cap) sums them itself.
+// A block takes tile order[blockIdx.x] = j * ntile + t (row j, bins from
+// t * NT * 64), or tile blockIdx.x itself without an order table.
 template <int NLEV, int NT>
 __global__ void __launch_bounds__(NT) k_harmsum_staged(
     const float* __restrict__ P, const float* __restrict__ Q4, int64_t nb, int Z, Thr thr,
+    const uint32_t* __restrict__ order, int64_t ntile,
     unsigned long long* __restrict__ list, unsigned int* nlist, int64_t cap,
     fdas_cand* __restrict__ out, unsigned long long* count, int64_t maxc) {
   constexpr int NQ = 1 << (NLEV - 1);
   extern __shared__ __align__(16) float stage[];  // per warp: 3 rotating buffers
-  const int j = blockIdx.y;
+  const int64_t tile = order ? (int64_t)order[blockIdx.x] : (int64_t)blockIdx.x;
+  const int j = (int)(tile / ntile);
+  const int64_t t = tile - (int64_t)j * ntile;
   const int warp = threadIdx.x >> 5;
   HsCtx x;
   x.stage = stage + warp * 3 * kStageW;
   x.Q4 = Q4;
   x.nq = nb >> 2;
-  x.R0w = (int64_t)blockIdx.x * (NT * kHsCells) + (int64_t)kWarpSpan * warp;
+  x.R0w = t * (NT * kHsCells) + (int64_t)kWarpSpan * warp;
   x.lane = threadIdx.x & 31;
   x.zc = (Z - 1) / 2;
   const int jc = j - x.zc;
@@ -340,10 +349,11 @@ int hs_launch(fdas_plan* p, const float* d_plane, const float* d_q4, fdas_cand* 
   e = cudaMemsetAsync(p->hs_nlist, 0, sizeof(unsigned int), p->stream);
   if (e != cudaSuccess) return cuda_check(e, "memset flagged-pair count");
   const int64_t w = plane_width(p);
-  dim3 grid((unsigned)((w + NT * kHsCells - 1) / (NT * kHsCells)), p->Z);
-  k_harmsum_staged<NLEV, NT><<<grid, NT, hs_smem<NT>(), p->stream>>>(
-      d_plane, d_q4, w, p->Z, thresholds_of(p), p->hs_list, p->hs_nlist, kHsListCap, d_out,
-      d_count, p->max_cands);
+  const int64_t ntile = (w + NT * kHsCells - 1) / (NT * kHsCells);
+  const uint32_t* order = p->hs_order_w == w ? p->hs_order[NT == 256 ? 0 : 1] : nullptr;
+  k_harmsum_staged<NLEV, NT><<<(unsigned)(ntile * p->Z), NT, hs_smem<NT>(), p->stream>>>(
+      d_plane, d_q4, w, p->Z, thresholds_of(p), order, ntile, p->hs_list, p->hs_nlist,
+      kHsListCap, d_out, d_count, p->max_cands);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(e, "k_harmsum_staged");
   int sms = 0;
@@ -367,6 +377,60 @@ int hs_dispatch(fdas_plan* p, const float* d_plane, const float* d_q4, fdas_cand
 }
 
 }  // namespace
+
+// The screen's tile order: ascending angle (j - zc) / (t + 1/2) about the
+// centre row. The sub-harmonic cells of top cell (j, r) lie near the ray
+// from (zc, 0) through it, at (zc + q (j - zc)/16, q r/16), so tiles of one
+// angle share the 4-bin maxima they read; run together they take them from
+// DRAM about once (an LRU model of the 126 MB L2 at the 2^23-sample,
+// 201-row size: 0.84 GB of DRAM reads, the size of the maxima, against
+// 2.2 GB row by row). Made on the host for the current plane width at plan
+// set-up, outside any stream capture; a launch whose width differs uses
+// the row-by-row order.
+void free_hs_order(fdas_plan* p) {
+  for (int k = 0; k < 2; ++k) {
+    if (p->hs_order[k]) cudaFree(p->hs_order[k]);
+    p->hs_order[k] = nullptr;
+  }
+  p->hs_order_w = 0;
+}
+
+int make_hs_order(fdas_plan* p) {
+  const int64_t w = plane_width(p);
+  if (p->hs_order[0] && p->hs_order_w == w) return FDAS_OK;
+  for (int k = 0; k < 2; ++k)
+    if (p->hs_order[k]) {
+      const int NT = k == 0 ? 256 : 128;
+      const int64_t ntile = (p->hs_order_w + NT * kHsCells - 1) / (NT * kHsCells);
+      p->device_bytes -= (int64_t)sizeof(uint32_t) * ntile * p->Z;
+    }
+  free_hs_order(p);
+  const int zc = (p->Z - 1) / 2;
+  for (int k = 0; k < 2; ++k) {
+    const int NT = k == 0 ? 256 : 128;
+    const int64_t ntile = (w + NT * kHsCells - 1) / (NT * kHsCells);
+    const int64_t n = ntile * p->Z;
+    if (n > (int64_t)UINT32_MAX) return FDAS_OK;  // row-by-row order
+    std::vector<uint32_t> ord((size_t)n);
+    std::iota(ord.begin(), ord.end(), 0u);
+    std::sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) {
+      const int64_t ja = a / ntile, ta = a - ja * ntile, jb = b / ntile, tb = b - jb * ntile;
+      // compare (ja - zc) / (ta + 1/2) with (jb - zc) / (tb + 1/2) exactly
+      const int64_t l = (ja - zc) * (2 * tb + 1), r = (jb - zc) * (2 * ta + 1);
+      if (l != r) return l < r;
+      return ta != tb ? ta < tb : ja < jb;
+    });
+    uint32_t* d = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d, sizeof(uint32_t) * (size_t)n);
+    if (e != cudaSuccess) return set_error(FDAS_ERR_NOMEM, "tile order table");
+    p->hs_order[k] = d;
+    p->device_bytes += (int64_t)sizeof(uint32_t) * n;
+    e = cudaMemcpy(d, ord.data(), sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_check(e, "tile order upload");
+  }
+  p->hs_order_w = w;
+  return FDAS_OK;
+}
 
 int launch_harmsum(fdas_plan* p, const float* d_plane, const float* d_q4, fdas_cand* d_out,
                    unsigned long long* d_count) {

@@ -49,6 +49,10 @@ struct fdas_plan {
   // exact sums (kHsListCap entries; flags past the capacity are summed inline)
   unsigned long long* hs_list = nullptr;
   unsigned int* hs_nlist = nullptr;
+  // launch order of the screen's tiles for 256- and 128-thread blocks,
+  // made for plane width hs_order_w (see make_hs_order)
+  uint32_t* hs_order[2] = {nullptr, nullptr};
+  int64_t hs_order_w = 0;
 
   // tensor-core correlation (precision variant); corr_mode = FDAS_CORR_*
   int corr_mode = 0;
@@ -133,5 +137,7 @@ int launch_pool4(fdas_plan* p, const float* d_plane, float* d_q4, fdas_cand* d_o
                  unsigned long long* d_count);
 int launch_harmsum(fdas_plan* p, const float* d_plane, const float* d_q4, fdas_cand* d_out,
                    unsigned long long* d_count);
+int make_hs_order(fdas_plan* p);
+void free_hs_order(fdas_plan* p);
 
 }  // namespace fdas
