@@ -79,8 +79,11 @@ int dalloc(fdas_plan* p, T** ptr, size_t count) {
   return FDAS_OK;
 }
 
+void free_lane(fdas_plan* p);
+
 void free_plan(fdas_plan* p) {
   if (!p) return;
+  free_lane(p);
   for (int b = 0; b < 2; ++b) {
     if (p->ev_in[b]) cudaEventDestroy(p->ev_in[b]);
     if (p->ev_done[b]) cudaEventDestroy(p->ev_done[b]);
@@ -199,6 +202,88 @@ bool cand_less(const fdas_cand& a, const fdas_cand& b) {
   return a.z_idx < b.z_idx;
 }
 
+// ---------------------------------------------------------------------------
+// Second trial lane (multi-trial calls of the FFT correlation on integer-bin
+// planes). The lane is a copy of the plan whose per-trial workspaces, stream
+// and candidate list are its own; the templates, twiddle and tile-order
+// tables are the plan's (read-only during a search).
+// ---------------------------------------------------------------------------
+bool lanes_usable(const fdas_plan* p) {
+  return p->stream != nullptr && p->corr_mode == FDAS_CORR_FFT && !p->interbin;
+}
+
+void free_lane(fdas_plan* p) {
+  fdas_plan* l = p->lane;
+  if (!l) return;
+  if (l->stream) {
+    cudaStreamSynchronize(l->stream);
+    cudaStreamDestroy(l->stream);
+  }
+  void* ptrs[] = {l->series, l->zbuf, l->spec, l->spec2, l->white, l->seg, l->plane,
+                  l->q4, l->cands, l->count, l->hs_list, l->hs_nlist};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  p->ev_fork = p->ev_join = nullptr;
+  p->device_bytes -= l->device_bytes;
+  delete l;
+  p->lane = nullptr;
+}
+
+// The lane for the plan's current shape, made or remade as needed, with the
+// plan's shared fields copied in.
+int ensure_lane(fdas_plan* p) {
+  const int64_t key[5] = {p->N, p->Z, (int64_t)p->S * p->L, p->max_cands, plane_width(p)};
+  if (p->lane && !std::equal(key, key + 5, p->lane_key)) free_lane(p);
+  if (!p->lane) {
+    fdas_plan* l = new fdas_plan(*p);
+    // nothing the plan owns may be freed through the lane
+    l->series = nullptr; l->zbuf = nullptr; l->spec = nullptr; l->spec2 = nullptr;
+    l->white = nullptr; l->seg = nullptr; l->plane = nullptr; l->q4 = nullptr;
+    l->cands = nullptr; l->count = nullptr; l->hs_list = nullptr; l->hs_nlist = nullptr;
+    l->stream = nullptr; l->lane = nullptr; l->device_bytes = 0;
+    p->lane = l;
+    int rc = 0;
+    if (!rc) rc = dalloc(l, &l->series, (size_t)p->N);
+    if (!rc) rc = dalloc(l, &l->zbuf, (size_t)p->M);
+    if (!rc) rc = dalloc(l, &l->spec, (size_t)p->nb);
+    if (!rc) rc = dalloc(l, &l->spec2, (size_t)p->M);
+    if (!rc) rc = dalloc(l, &l->white, (size_t)p->nb);
+    if (!rc) rc = dalloc(l, &l->seg, (size_t)p->S * p->L);
+    if (!rc) rc = dalloc(l, &l->plane, (size_t)p->Z * plane_width(p));
+    if (!rc) rc = dalloc(l, &l->q4, (size_t)p->Z * plane_width(p) / 4);
+    if (!rc) rc = dalloc(l, &l->cands, (size_t)p->max_cands);
+    if (!rc) rc = dalloc(l, &l->count, 1);
+    if (!rc) rc = dalloc(l, &l->hs_list, (size_t)kHsListCap);
+    if (!rc) rc = dalloc(l, &l->hs_nlist, 1);
+    if (!rc)
+      rc = cuda_check(cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking), "lane stream");
+    if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming), "event");
+    if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming), "event");
+    p->device_bytes += l->device_bytes;
+    if (rc) {
+      free_lane(p);
+      return rc;
+    }
+    std::copy(key, key + 5, p->lane_key);
+  }
+  // shared fields (modes, tables, templates) as the plan has them now
+  fdas_plan* l = p->lane;
+  fdas_plan own = *l;
+  *l = *p;
+  l->series = own.series; l->zbuf = own.zbuf; l->spec = own.spec; l->spec2 = own.spec2;
+  l->white = own.white; l->seg = own.seg; l->plane = own.plane; l->q4 = own.q4;
+  l->plane_cap = (int64_t)p->Z * plane_width(p);
+  l->cands = own.cands; l->count = own.count; l->hs_list = own.hs_list;
+  l->hs_nlist = own.hs_nlist; l->stream = own.stream; l->device_bytes = own.device_bytes;
+  l->series2 = nullptr; l->cands2 = nullptr; l->count2 = nullptr; l->cstream = nullptr;
+  l->ev_in[0] = l->ev_in[1] = l->ev_done[0] = l->ev_done[1] = nullptr;
+  l->lane = nullptr; l->ev_fork = l->ev_join = nullptr;
+  l->dkeys = nullptr; l->dvals = nullptr; l->dbits = 0;
+  return FDAS_OK;
+}
+
 int search_impl(fdas_plan* p, const float* d_series, int32_t n_trials, fdas_cand* h_out,
                 int64_t* h_counts) {
   bool overflow = false;
@@ -252,9 +337,22 @@ int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_ca
     }
     if (rc) return rc;
   }
-  float* buf[2] = {p->series, p->series2};
-  fdas_cand* cbuf[2] = {p->cands, p->cands2};
-  unsigned long long* nbuf[2] = {p->count, p->count2};
+  // trial t runs on lane t % 2: the plan itself, then the second lane (its
+  // own workspaces and stream) where usable, else the plan again with the
+  // second staging and candidate buffers
+  fdas_plan* q[2] = {p, p};
+  if (lanes_usable(p)) {
+    if ((rc = ensure_lane(p))) return rc;
+    q[1] = p->lane;
+  }
+  float* buf[2] = {p->series, q[1] != p ? q[1]->series : p->series2};
+  fdas_cand* cbuf[2] = {p->cands, q[1] != p ? q[1]->cands : p->cands2};
+  unsigned long long* nbuf[2] = {p->count, q[1] != p ? q[1]->count : p->count2};
+  if (q[1] != p) {  // the lane starts after the caller's work on the plan stream
+    rc = cuda_check(cudaEventRecord(p->ev_fork, p->stream), "event");
+    if (!rc) rc = cuda_check(cudaStreamWaitEvent(q[1]->stream, p->ev_fork, 0), "wait");
+    if (rc) return rc;
+  }
   const size_t bytes = sizeof(float) * (size_t)p->N;
   bool overflow = false;
   // read back and sort trial t (its kernels are done once ev_done fires)
@@ -289,8 +387,8 @@ int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_ca
   for (int32_t t = 0; t < n_trials && !rc; ++t) {
     const int b = t & 1, o = b ^ 1;
     if (d_series) {
-      rc = run_trial(p, d_series + (size_t)t * p->N, cbuf[b], nbuf[b]);
-      if (!rc) rc = cuda_check(cudaEventRecord(p->ev_done[b], p->stream), "event");
+      rc = run_trial(q[b], d_series + (size_t)t * p->N, cbuf[b], nbuf[b]);
+      if (!rc) rc = cuda_check(cudaEventRecord(p->ev_done[b], q[b]->stream), "event");
       if (!rc && t >= 1) rc = finish(t - 1);
       continue;
     }
@@ -303,18 +401,23 @@ int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_ca
                         "copy series");
       if (!rc) rc = cuda_check(cudaEventRecord(p->ev_in[o], p->cstream), "event");
     }
-    if (!rc) rc = cuda_check(cudaStreamWaitEvent(p->stream, p->ev_in[b], 0), "wait");
-    if (!rc) rc = run_trial(p, buf[b], cbuf[b], nbuf[b]);
-    if (!rc) rc = cuda_check(cudaEventRecord(p->ev_done[b], p->stream), "event");
+    if (!rc) rc = cuda_check(cudaStreamWaitEvent(q[b]->stream, p->ev_in[b], 0), "wait");
+    if (!rc) rc = run_trial(q[b], buf[b], cbuf[b], nbuf[b]);
+    if (!rc) rc = cuda_check(cudaEventRecord(p->ev_done[b], q[b]->stream), "event");
     // the host reads back trial t-1 while trial t runs; trial t+1 reuses
     // its candidate buffer only after this returns
     if (!rc && t >= 1) rc = finish(t - 1);
   }
   if (!rc && n_trials >= 1) rc = finish(n_trials - 1);
+  if (!rc && q[1] != p) {  // the plan stream continues after the lane's work
+    rc = cuda_check(cudaEventRecord(p->ev_join, q[1]->stream), "event");
+    if (!rc) rc = cuda_check(cudaStreamWaitEvent(p->stream, p->ev_join, 0), "wait");
+  }
   if (!rc) rc = gemm_status(p);
   if (rc) {
     cudaStreamSynchronize(p->cstream);
     cudaStreamSynchronize(p->stream);
+    if (q[1] != p) cudaStreamSynchronize(q[1]->stream);
     return rc;
   }
   return overflow ? set_error(FDAS_ERR_OVERFLOW, "candidate list overflow") : FDAS_OK;
@@ -469,9 +572,24 @@ int fdas_search_device(fdas_plan* p, const float* d_series, int32_t n_trials, fd
                        int64_t* d_counts) {
   if (!p || !d_series || n_trials < 0 || (n_trials > 0 && (!d_out || !d_counts)))
     return set_error(FDAS_ERR_INVALID, "bad argument to fdas_search_device");
+  fdas_plan* q[2] = {p, p};
+  if (n_trials > 1 && lanes_usable(p)) {
+    // odd trials on the second lane: it starts after the caller's work on
+    // the plan stream, which continues once both lanes are done
+    int rc = ensure_lane(p);
+    if (!rc) rc = cuda_check(cudaEventRecord(p->ev_fork, p->stream), "event");
+    if (!rc) rc = cuda_check(cudaStreamWaitEvent(p->lane->stream, p->ev_fork, 0), "wait");
+    if (rc) return rc;
+    q[1] = p->lane;
+  }
   for (int32_t t = 0; t < n_trials; ++t) {
-    int rc = run_trial(p, d_series + (size_t)t * p->N, d_out + (size_t)t * p->max_cands,
+    int rc = run_trial(q[t & 1], d_series + (size_t)t * p->N, d_out + (size_t)t * p->max_cands,
                        reinterpret_cast<unsigned long long*>(d_counts + t));
+    if (rc) return rc;
+  }
+  if (q[1] != p) {
+    int rc = cuda_check(cudaEventRecord(p->ev_join, q[1]->stream), "event");
+    if (!rc) rc = cuda_check(cudaStreamWaitEvent(p->stream, p->ev_join, 0), "wait");
     if (rc) return rc;
   }
   return FDAS_OK;
@@ -687,6 +805,8 @@ int batch_view(fdas_batch* b, int64_t N, fdas_plan** out) {
   v->tw_M1 = v->tw_M2 = v->tw4_lo = v->tw4_hi = v->twN_lo = v->twN_hi = nullptr;
   v->hs_order[0] = v->hs_order[1] = nullptr;
   v->hs_order_w = 0;
+  v->lane = nullptr;  // batches run one trial after another on the base stream
+  v->ev_fork = v->ev_join = nullptr;
   v->device_bytes = 0;
   int rc = set_geometry(v, N);
   if (!rc) rc = alloc_geometry_tables(v);

@@ -80,6 +80,14 @@ struct fdas_plan {
   cudaEvent_t ev_in[2] = {nullptr, nullptr};    // series copy landed
   cudaEvent_t ev_done[2] = {nullptr, nullptr};  // trial finished on the plan stream
 
+  // second trial lane of multi-trial calls: a plan that shares this plan's
+  // read-only tables and owns its own per-trial workspaces and stream, so
+  // that trials t and t + 1 overlap on the GPU (made on first use); fork and
+  // join events order it after and before this plan's stream
+  fdas_plan* lane = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int64_t lane_key[5] = {0, 0, 0, 0, 0};  // N, Z, S * L, max_cands, plane width it was made for
+
   int64_t device_bytes = 0;
   int corr_ctas_per_sm = 0;  // launch shape of the correlation kernel (last launch)
   int corr_grid = 0;
