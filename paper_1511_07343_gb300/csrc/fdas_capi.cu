@@ -267,6 +267,7 @@ int ensure_lane(fdas_plan* p) {
       return rc;
     }
     std::copy(key, key + 5, p->lane_key);
+    ++p->lane_gen;
   }
   // shared fields (modes, tables, templates) as the plan has them now
   fdas_plan* l = p->lane;
@@ -779,6 +780,7 @@ struct fdas_batch {
   std::vector<int64_t> key_N;
   fdas_cand* key_out = nullptr;
   int64_t* key_counts = nullptr;
+  int64_t key_lane_gen = 0;  // the base's trial lane the graph was captured with (0: none)
   int64_t graph_builds = 0, graph_launches = 0;
   // autotuner record
   int n_tuned = 0;
@@ -855,14 +857,36 @@ int time_segment(int64_t N, int32_t zmax, int32_t dz, int32_t m, int32_t L, int3
 }
 
 // Trials of a batch in order, launched directly on the plan's stream.
-int batch_direct(const std::vector<fdas_plan*>& vs, const float* const* d_series,
-                 fdas_cand* d_out, int64_t* d_counts) {
-  for (size_t t = 0; t < vs.size(); ++t) {
-    int rc = run_trial(vs[t], d_series[t], d_out + t * vs[t]->max_cands,
-                       reinterpret_cast<unsigned long long*>(d_counts + t));
-    if (rc) return rc;
+// The trials of a batch in order; with a lane (base->lane, made before any
+// capture), odd trials run on it: their length's view with the lane's
+// workspaces and stream, forked from and joined to the base stream.
+int batch_direct(fdas_plan* base, const std::vector<fdas_plan*>& vs,
+                 const float* const* d_series, fdas_cand* d_out, int64_t* d_counts) {
+  fdas_plan* lane = vs.size() > 1 && lanes_usable(base) ? base->lane : nullptr;
+  int rc = FDAS_OK;
+  if (lane) {
+    rc = cuda_check(cudaEventRecord(base->ev_fork, base->stream), "event");
+    if (!rc) rc = cuda_check(cudaStreamWaitEvent(lane->stream, base->ev_fork, 0), "wait");
   }
-  return FDAS_OK;
+  for (size_t t = 0; t < vs.size() && !rc; ++t) {
+    fdas_cand* out = d_out + t * vs[t]->max_cands;
+    auto* cnt = reinterpret_cast<unsigned long long*>(d_counts + t);
+    if (lane && (t & 1)) {
+      fdas_plan lv = *vs[t];  // this length's geometry and tables
+      lv.series = lane->series; lv.zbuf = lane->zbuf; lv.spec = lane->spec;
+      lv.spec2 = lane->spec2; lv.white = lane->white; lv.seg = lane->seg;
+      lv.plane = lane->plane; lv.q4 = lane->q4; lv.hs_list = lane->hs_list;
+      lv.hs_nlist = lane->hs_nlist; lv.stream = lane->stream;
+      rc = run_trial(&lv, d_series[t], out, cnt);
+    } else {
+      rc = run_trial(vs[t], d_series[t], out, cnt);
+    }
+  }
+  if (!rc && lane) {
+    rc = cuda_check(cudaEventRecord(base->ev_join, lane->stream), "event");
+    if (!rc) rc = cuda_check(cudaStreamWaitEvent(base->stream, base->ev_join, 0), "wait");
+  }
+  return rc;
 }
 
 }  // namespace
@@ -982,10 +1006,16 @@ int fdas_search_batch(fdas_batch* b, const float* const* d_series, const int64_t
     int rc = batch_view(b, N[t], &vs[t]);
     if (rc) return rc;
   }
+  if (n_trials > 1 && lanes_usable(b->base)) {
+    int rc = ensure_lane(b->base);
+    if (rc) return rc;
+  }
   cudaStream_t s = b->base->stream;
   // the legacy default stream cannot be captured
-  if (!b->graphs || s == nullptr || n_trials == 0) return batch_direct(vs, d_series, d_out, d_counts);
+  if (!b->graphs || s == nullptr || n_trials == 0)
+    return batch_direct(b->base, vs, d_series, d_out, d_counts);
   const bool same = b->exec && b->key_out == d_out && b->key_counts == d_counts &&
+                    b->key_lane_gen == (b->base->lane ? b->base->lane_gen : 0) &&
                     b->key_series.size() == (size_t)n_trials &&
                     std::equal(b->key_series.begin(), b->key_series.end(), d_series) &&
                     std::equal(b->key_N.begin(), b->key_N.end(), N);
@@ -993,7 +1023,7 @@ int fdas_search_batch(fdas_batch* b, const float* const* d_series, const int64_t
     int rc = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal),
                         "begin capture");
     if (rc) return rc;
-    const int trc = batch_direct(vs, d_series, d_out, d_counts);
+    const int trc = batch_direct(b->base, vs, d_series, d_out, d_counts);
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(s, &g);
     if (trc || ce != cudaSuccess) {
@@ -1022,6 +1052,7 @@ int fdas_search_batch(fdas_batch* b, const float* const* d_series, const int64_t
     b->key_N.assign(N, N + n_trials);
     b->key_out = d_out;
     b->key_counts = d_counts;
+    b->key_lane_gen = b->base->lane ? b->base->lane_gen : 0;
   }
   ++b->graph_launches;
   return cuda_check(cudaGraphLaunch(b->exec, s), "graph launch");
