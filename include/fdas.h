@@ -118,6 +118,20 @@ int fdas_search_host(fdas_plan* plan, const float* h_series, int32_t n_trials,
 int fdas_search_device(fdas_plan* plan, const float* d_series, int32_t n_trials,
                        fdas_cand* d_out, int64_t* d_counts);
 
+/* Trial lanes. When fdas_search, fdas_search_host, fdas_search_device or
+ * fdas_search_batch runs 2 or more trials on a stream other than the legacy
+ * default stream, with the FFT correlation on integer-bin planes, the odd
+ * trials run on a second lane of the plan: its own per-trial workspaces
+ * (series staging, spectra, segment spectra, plane, 4-bin maxima and lists;
+ * about 4N + 36N + 8 S L + 5 Z N/2 + 16 max_cands + 8 MiB bytes, 4.4 GB for
+ * N = 2^23, zmax = 200, L = 8192) and its own stream, sharing the plan's
+ * templates and tables, so that consecutive trials overlap on the GPU. The
+ * lane is forked from the plan stream at the start of the call and joined
+ * back at the end: work enqueued on the plan stream before the call is done
+ * before any trial starts, and work enqueued after it waits for every trial.
+ * The first such call allocates the lane (counted in device_bytes); it is
+ * remade if the plan's shape changes and freed with the plan. */
+
 /* Batches of DM trials of uneven length (series of different N).
  * fdas_batch_create makes one plan for the longest series N_max (same
  * arguments and limits as fdas_plan_create) whose workspaces and templates

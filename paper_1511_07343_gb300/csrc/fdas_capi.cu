@@ -108,6 +108,7 @@ int launch_plane(fdas_plan* p, float* d_plane, float* d_q4, fdas_cand* d_out,
 // The path for one trial; the plane goes to p->plane, candidates to d_out.
 int run_trial(fdas_plan* p, const float* d_x, fdas_cand* d_out, unsigned long long* d_count) {
   int rc;
+  p->last_on_lane = false;
   if ((rc = cuda_check(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), p->stream),
                        "memset count")))
     return rc;
@@ -413,6 +414,7 @@ int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_ca
   if (!rc && q[1] != p) {  // the plan stream continues after the lane's work
     rc = cuda_check(cudaEventRecord(p->ev_join, q[1]->stream), "event");
     if (!rc) rc = cuda_check(cudaStreamWaitEvent(p->stream, p->ev_join, 0), "wait");
+    p->last_on_lane = n_trials >= 2 && ((n_trials - 1) & 1);
   }
   if (!rc) rc = gemm_status(p);
   if (rc) {
@@ -592,13 +594,17 @@ int fdas_search_device(fdas_plan* p, const float* d_series, int32_t n_trials, fd
     int rc = cuda_check(cudaEventRecord(p->ev_join, q[1]->stream), "event");
     if (!rc) rc = cuda_check(cudaStreamWaitEvent(p->stream, p->ev_join, 0), "wait");
     if (rc) return rc;
+    p->last_on_lane = (n_trials - 1) & 1;
   }
   return FDAS_OK;
 }
 
 int fdas_plane_debug(fdas_plan* p, float* d_plane) {
   if (!p || !d_plane) return set_error(FDAS_ERR_INVALID, "NULL argument");
-  return cuda_check(cudaMemcpyAsync(d_plane, p->plane, sizeof(float) * (size_t)p->Z * plane_width(p),
+  // the lane's plane if the last trial ran there (its work is ordered
+  // before the plan stream's by the join of that call)
+  const float* src = p->last_on_lane && p->lane ? p->lane->plane : p->plane;
+  return cuda_check(cudaMemcpyAsync(d_plane, src, sizeof(float) * (size_t)p->Z * plane_width(p),
                                     cudaMemcpyDeviceToDevice, p->stream),
                     "copy plane");
 }
@@ -731,6 +737,7 @@ int fdas_profile_trial(fdas_plan* p, const float* d_series, float* h_ms) {
       return set_error(FDAS_ERR_CUDA, "cudaEventCreate failed");
     }
   }
+  p->last_on_lane = false;
   int rc = cuda_check(cudaMemsetAsync(p->count, 0, sizeof(unsigned long long), p->stream),
                       "memset count");
   if (!rc) rc = cuda_check(cudaEventRecord(ev[0], p->stream), "event");

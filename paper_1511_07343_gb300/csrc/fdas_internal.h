@@ -88,6 +88,7 @@ struct fdas_plan {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int64_t lane_key[5] = {0, 0, 0, 0, 0};  // N, Z, S * L, max_cands, plane width it was made for
   int64_t lane_gen = 0;                    // lanes made so far (a captured graph names its lane)
+  bool last_on_lane = false;               // the last trial of this plan ran on the lane
 
   int64_t device_bytes = 0;
   int corr_ctas_per_sm = 0;  // launch shape of the correlation kernel (last launch)

@@ -309,6 +309,45 @@ def test_batch_host_device_paths_agree(gpu_lib):
         assert keys(dev[t * M: t * M + dcnt[t]]) == single[t]
 
 
+@pytest.mark.parametrize("n_trials", [2, 3])
+def test_trial_lanes_match_single_trials(gpu_lib, n_trials):
+    """Multi-trial calls run odd trials on the plan's second lane: every
+    trial's candidates equal a single-trial call's, and the debug plane is
+    the last trial's whichever lane ran it."""
+    fd = gpu_lib
+    N = 1 << 15
+    xs = np.stack([make_series(N, 500 + t, [Chirp(3000.0 + 700 * t, -4.0 * t, 9.0, 0.3, 4)])
+                   for t in range(n_trials)])
+    stream = torch.cuda.Stream(DEV)  # lanes need a stream other than the legacy default one
+    plan = fd.fdas_plan_create(N, 30, 2, 128, 2048, 8, 6.0, 4096, stream.cuda_stream)
+    try:
+        info = fd.fdas_plan_get_info(plan)
+        single, planes = [], []
+        for t in range(n_trials):
+            got, _ = search_one(fd, plan, info, xs[t])
+            single.append(keys(got))
+            planes.append(gpu_plane(fd, plan, info))
+        bytes_before = fd.fdas_plan_get_info(plan).device_bytes
+        d_x = torch.from_numpy(xs.ravel()).to(DEV)
+        d_out = torch.empty(n_trials * info.max_cands * 4, dtype=torch.int32, device=DEV)
+        d_cnt = torch.zeros(n_trials, dtype=torch.int64, device=DEV)
+        torch.cuda.synchronize()
+        fd.fdas_search_device(plan, d_x, n_trials, d_out, d_cnt)
+        last_plane = gpu_plane(fd, plan, info)
+        torch.cuda.synchronize()
+        bytes_after = fd.fdas_plan_get_info(plan).device_bytes
+        dev = d_out.cpu().numpy().view(fd.CAND_DTYPE)
+        dcnt = d_cnt.cpu().numpy()
+    finally:
+        fd.fdas_plan_destroy(plan)
+    M = info.max_cands
+    for t in range(n_trials):
+        assert single[t]
+        assert keys(dev[t * M: t * M + dcnt[t]]) == single[t]
+    assert np.array_equal(last_plane, planes[-1])
+    assert bytes_after > bytes_before  # the lane's workspaces are counted
+
+
 def test_candidate_overflow_reports_exact_count(gpu_lib):
     fd = gpu_lib
     N = 1 << 14
