@@ -262,9 +262,10 @@ __global__ void __launch_bounds__(NT) k_harmsum_staged(
     fdas_cand* __restrict__ out, unsigned long long* count, int64_t maxc) {
   constexpr int NQ = 1 << (NLEV - 1);
   extern __shared__ __align__(16) float stage[];  // per warp: 3 rotating buffers
-  const int64_t tile = order ? (int64_t)order[blockIdx.x] : (int64_t)blockIdx.x;
-  const int j = (int)(tile / ntile);
-  const int64_t t = tile - (int64_t)j * ntile;
+  // tile ids are below 2^32 (the order tables exist only then)
+  const uint32_t tile = order ? __ldg(order + blockIdx.x) : blockIdx.x;
+  const int j = (int)(tile / (uint32_t)ntile);
+  const int64_t t = (int64_t)(tile - (uint32_t)j * (uint32_t)ntile);
   const int warp = threadIdx.x >> 5;
   HsCtx x;
   x.stage = stage + warp * 3 * kStageW;
