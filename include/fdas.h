@@ -159,8 +159,8 @@ int fdas_search_batch(fdas_batch* batch, const float* const* d_series, const int
 int fdas_batch_set_graphs(fdas_batch* batch, int32_t enable);
 
 /* Autotuned batch: times one trial of every combination of segment length
- * L in {2048, 4096, 8192} with L >= 2m and harmonic-sum block of 256 or 128
- * threads (16384 or 8192 top bins per block) on a probe series of N_max
+ * L in {2048, 4096, 8192} with L >= 2m and harmonic-sum block of 256 or 32
+ * threads (16384 or 2048 top bins per block) on a probe series of N_max
  * samples (d_probe, device; NULL = seeded Gaussian white noise made on the
  * device), on a fresh plan per L (median of 3 after a warm-up), and creates
  * the batch with the fastest. L sets the segment FFT size, the number of

@@ -930,7 +930,7 @@ int fdas_batch_create_tuned(fdas_batch** out, int64_t N_max, int32_t zmax, int32
     rc = launch_probe_noise(own, N_max, 0x5eedull, s);
     d_probe = own;
   }
-  const int hs[2] = {256, 128};  // harmonic-sum block sizes
+  const int hs[2] = {256, 32};  // harmonic-sum block sizes
   int n = 0, best = -1;
   int32_t Ls[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   float ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};

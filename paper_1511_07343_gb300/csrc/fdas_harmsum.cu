@@ -78,6 +78,12 @@ __host__ __device__ constexpr int kq(int q, int i) { return (2 * q * i + 16) >> 
 constexpr int kHsCells = 64;                  // top bins per lane
 constexpr int kHsPairs = kHsCells / 2;        // bin pairs per lane
 constexpr int kWarpSpan = 32 * kHsCells;      // top bins per warp
+// block sizes of the screen (threads) and their order tables: one-warp
+// blocks are the default (each warp retires on its own and a block fits
+// beside the correlation kernel's); 256 is the alternative the batch
+// autotuner times
+constexpr int kHsBlocks[2] = {256, 32};
+constexpr int hs_block_index(int nt) { return nt == 256 ? 0 : 1; }
 // last group offset a lane reads for fraction q, groups staged per warp
 __host__ __device__ constexpr int omax(int q) { return kq(q, kHsCells - 1) >> 2; }
 __host__ __device__ constexpr int nchunk(int q) {
@@ -255,7 +261,7 @@ FDAS_DEV void hs_exact_pair(const float* __restrict__ P, int64_t nb, int j, int 
 // A block takes tile order[blockIdx.x] = j * ntile + t (row j, bins from
 // t * NT * 64), or tile blockIdx.x itself without an order table.
 template <int NLEV, int NT>
-__global__ void __launch_bounds__(NT) k_harmsum_staged(
+__global__ void __launch_bounds__(NT, NT == 32 ? 32 : 0) k_harmsum_staged(
     const float* __restrict__ P, const float* __restrict__ Q4, int64_t nb, int Z, Thr thr,
     const uint32_t* __restrict__ order, int64_t ntile,
     unsigned long long* __restrict__ list, unsigned int* nlist, int64_t cap,
@@ -351,7 +357,7 @@ int hs_launch(fdas_plan* p, const float* d_plane, const float* d_q4, fdas_cand* 
   if (e != cudaSuccess) return cuda_check(e, "memset flagged-pair count");
   const int64_t w = plane_width(p);
   const int64_t ntile = (w + NT * kHsCells - 1) / (NT * kHsCells);
-  const uint32_t* order = p->hs_order_w == w ? p->hs_order[NT == 256 ? 0 : 1] : nullptr;
+  const uint32_t* order = p->hs_order_w == w ? p->hs_order[hs_block_index(NT)] : nullptr;
   k_harmsum_staged<NLEV, NT><<<(unsigned)(ntile * p->Z), NT, hs_smem<NT>(), p->stream>>>(
       d_plane, d_q4, w, p->Z, thresholds_of(p), order, ntile, p->hs_list, p->hs_nlist,
       kHsListCap, d_out, d_count, p->max_cands);
@@ -401,14 +407,14 @@ int make_hs_order(fdas_plan* p) {
   if (p->hs_order[0] && p->hs_order_w == w) return FDAS_OK;
   for (int k = 0; k < 2; ++k)
     if (p->hs_order[k]) {
-      const int NT = k == 0 ? 256 : 128;
+      const int NT = kHsBlocks[k];
       const int64_t ntile = (p->hs_order_w + NT * kHsCells - 1) / (NT * kHsCells);
       p->device_bytes -= (int64_t)sizeof(uint32_t) * ntile * p->Z;
     }
   free_hs_order(p);
   const int zc = (p->Z - 1) / 2;
   for (int k = 0; k < 2; ++k) {
-    const int NT = k == 0 ? 256 : 128;
+    const int NT = kHsBlocks[k];
     const int64_t ntile = (w + NT * kHsCells - 1) / (NT * kHsCells);
     const int64_t n = ntile * p->Z;
     if (n > (int64_t)UINT32_MAX) return FDAS_OK;  // row-by-row order
@@ -436,8 +442,8 @@ int make_hs_order(fdas_plan* p) {
 int launch_harmsum(fdas_plan* p, const float* d_plane, const float* d_q4, fdas_cand* d_out,
                    unsigned long long* d_count) {
   if (p->n_levels < 2) return FDAS_OK;
-  return p->hs_threads == 128 ? hs_dispatch<128>(p, d_plane, d_q4, d_out, d_count)
-                              : hs_dispatch<256>(p, d_plane, d_q4, d_out, d_count);
+  return p->hs_threads == 256 ? hs_dispatch<256>(p, d_plane, d_q4, d_out, d_count)
+                              : hs_dispatch<32>(p, d_plane, d_q4, d_out, d_count);
 }
 
 }  // namespace fdas

@@ -49,15 +49,15 @@ struct fdas_plan {
   // exact sums (kHsListCap entries; flags past the capacity are summed inline)
   unsigned long long* hs_list = nullptr;
   unsigned int* hs_nlist = nullptr;
-  // launch order of the screen's tiles for 256- and 128-thread blocks,
-  // made for plane width hs_order_w (see make_hs_order)
+  // launch order of the screen's tiles for 256- and 32-thread blocks, made
+  // for plane width hs_order_w (see make_hs_order)
   uint32_t* hs_order[2] = {nullptr, nullptr};
   int64_t hs_order_w = 0;
 
   // tensor-core correlation (precision variant); corr_mode = FDAS_CORR_*
   int corr_mode = 0;
   int whiten_mode = 0;         // FDAS_WHITEN_*
-  int hs_threads = 256;        // harmonic-sum block (128 or 256 threads)
+  int hs_threads = 32;         // harmonic-sum block (32 or 256 threads)
   // half-bin planes: taps and spectra of 2Z template rows (row 2j + e at
   // frequency offset e/2); the plane and Q4 then have 2 nb columns
   int interbin = 0;

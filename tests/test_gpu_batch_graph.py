@@ -91,7 +91,7 @@ def test_tuned_batch_picks_the_fastest_segment(gpu_lib):
         info = fd.fdas_batch_get_info(batch)
         assert info.n_tuned == 6
         assert list(info.tuned_segment[:6]) == [2048, 2048, 4096, 4096, 8192, 8192]
-        assert list(info.tuned_hs_block[:6]) == [256, 128] * 3
+        assert list(info.tuned_hs_block[:6]) == [256, 32] * 3
         ms = list(info.tuned_ms[:6])
         assert all(t > 0 for t in ms)
         best = int(np.argmin(ms))
