@@ -96,7 +96,8 @@ int fdas_plan_get_info(const fdas_plan* plan, fdas_plan_info* info);
  * FDAS_ERR_OVERFLOW after finishing every trial. Synchronises the stream.
  * With n_trials > 1 on a stream other than the legacy default stream, trial
  * t-1's candidates are read back and sorted while trial t runs (a second
- * candidate list, allocated on first use, alternates with the first). */
+ * candidate list alternates with the first: the second trial lane's, see
+ * below, or one allocated on first use). */
 int fdas_search(fdas_plan* plan, const float* d_series, int32_t n_trials,
                 fdas_cand* h_out, int64_t* h_counts);
 
@@ -106,8 +107,10 @@ int fdas_search(fdas_plan* plan, const float* d_series, int32_t n_trials,
  * kernels: series t+1 is copied in (on a copy stream of the plan, into a
  * second staging buffer) and trial t-1's candidates are read back and
  * sorted while trial t runs; page-locked host memory is needed for the
- * copies to overlap. The first such call allocates the second staging
- * buffer and candidate list (4N + 16 max_cands bytes). */
+ * copies to overlap. The second staging buffer and candidate list are the
+ * second trial lane's (below); where no lane is used (tensor-core or
+ * half-bin modes) the first such call allocates them (4N + 16 max_cands
+ * bytes). */
 int fdas_search_host(fdas_plan* plan, const float* h_series, int32_t n_trials,
                      fdas_cand* h_out, int64_t* h_counts);
 

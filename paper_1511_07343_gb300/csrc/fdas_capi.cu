@@ -324,11 +324,8 @@ int search_impl(fdas_plan* p, const float* d_series, int32_t n_trials, fdas_cand
 // copied in and only the read-back overlaps)
 int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_cand* h_out,
                   int64_t* h_counts, const float* d_series = nullptr) {
-  int rc;
-  if (!p->series2) {
-    if ((rc = dalloc(p, &p->series2, (size_t)p->N))) return rc;
-    if ((rc = dalloc(p, &p->cands2, (size_t)p->max_cands))) return rc;
-    if ((rc = dalloc(p, &p->count2, 1))) return rc;
+  int rc = FDAS_OK;
+  if (!p->cstream) {
     if ((rc = cuda_check(cudaStreamCreateWithFlags(&p->cstream, cudaStreamNonBlocking),
                          "copy stream")))
       return rc;
@@ -340,12 +337,16 @@ int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_ca
     if (rc) return rc;
   }
   // trial t runs on lane t % 2: the plan itself, then the second lane (its
-  // own workspaces and stream) where usable, else the plan again with the
-  // second staging and candidate buffers
+  // own workspaces and stream) where usable, else the plan again with a
+  // second staging buffer and candidate list of its own
   fdas_plan* q[2] = {p, p};
   if (lanes_usable(p)) {
     if ((rc = ensure_lane(p))) return rc;
     q[1] = p->lane;
+  } else if (!p->series2 || !p->cands2 || !p->count2) {
+    if (!p->series2 && (rc = dalloc(p, &p->series2, (size_t)p->N))) return rc;
+    if (!p->cands2 && (rc = dalloc(p, &p->cands2, (size_t)p->max_cands))) return rc;
+    if (!p->count2 && (rc = dalloc(p, &p->count2, 1))) return rc;
   }
   float* buf[2] = {p->series, q[1] != p ? q[1]->series : p->series2};
   fdas_cand* cbuf[2] = {p->cands, q[1] != p ? q[1]->cands : p->cands2};

@@ -264,7 +264,7 @@ template <int NLEV, int NT>
 __global__ void __launch_bounds__(NT, NT == 32 ? 32 : 0) k_harmsum_staged(
     const float* __restrict__ P, const float* __restrict__ Q4, int64_t nb, int Z, Thr thr,
     const uint32_t* __restrict__ order, int64_t ntile,
-    unsigned long long* __restrict__ list, unsigned int* nlist, int64_t cap,
+    unsigned long long* __restrict__ list, unsigned long long* nlist, int64_t cap,
     fdas_cand* __restrict__ out, unsigned long long* count, int64_t maxc) {
   constexpr int NQ = 1 << (NLEV - 1);
   extern __shared__ __align__(16) float stage[];  // per warp: 3 rotating buffers
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 32 : 0) k_harmsum_staged(
   else if (first + kHsCells > nb) pmask &= (1u << ((nb - first) >> 1)) - 1u;
   if (pmask == 0) return;
   const unsigned n = (unsigned)__popc(pmask);
-  const unsigned long long base = atomicAdd(nlist, n);
+  const unsigned long long base = atomicAdd(nlist, (unsigned long long)n);
   const unsigned long long key = (unsigned long long)j << 32;
   for (unsigned k = 0; pmask; ++k) {
     const int r = (int)(first + 2 * (__ffs(pmask) - 1));
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 32 : 0) k_harmsum_staged(
 template <int NLEV>
 __global__ void __launch_bounds__(256) k_harmsum_exact(
     const float* __restrict__ P, const unsigned long long* __restrict__ list,
-    const unsigned int* nlist, int64_t cap, int64_t nb, int Z, Thr thr,
+    const unsigned long long* nlist, int64_t cap, int64_t nb, int Z, Thr thr,
     fdas_cand* __restrict__ out, unsigned long long* count, int64_t maxc) {
   constexpr int NQ = 1 << (NLEV - 1);
   const int64_t n = min((int64_t)*nlist, cap);
@@ -353,7 +353,7 @@ int hs_launch(fdas_plan* p, const float* d_plane, const float* d_q4, fdas_cand* 
     if (e != cudaSuccess) return cuda_check(e, "k_harmsum_staged attr");
     attr_dev = dev;
   }
-  e = cudaMemsetAsync(p->hs_nlist, 0, sizeof(unsigned int), p->stream);
+  e = cudaMemsetAsync(p->hs_nlist, 0, sizeof(unsigned long long), p->stream);
   if (e != cudaSuccess) return cuda_check(e, "memset flagged-pair count");
   const int64_t w = plane_width(p);
   const int64_t ntile = (w + NT * kHsCells - 1) / (NT * kHsCells);

@@ -48,7 +48,7 @@ struct fdas_plan {
   // pairs of top bins the harmonic-sum screen flags, (j << 32) | r, for the
   // exact sums (kHsListCap entries; flags past the capacity are summed inline)
   unsigned long long* hs_list = nullptr;
-  unsigned int* hs_nlist = nullptr;
+  unsigned long long* hs_nlist = nullptr;
   // launch order of the screen's tiles for 256- and 32-thread blocks, made
   // for plane width hs_order_w (see make_hs_order)
   uint32_t* hs_order[2] = {nullptr, nullptr};
