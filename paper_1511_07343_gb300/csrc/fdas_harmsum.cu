@@ -67,8 +67,9 @@ __global__ void __launch_bounds__(256) k_pool4(const float* __restrict__ P, floa
 // next lane's first (a shuffle). Each pair's term is bounded by the maximum
 // of the (one or two) groups its two sub-harmonic bins fall in; float
 // addition is monotone, so a pair whose running bound stays below T_h holds
-// no candidate at level h. The rare flagged pairs are summed exactly from P
-// in the same order and compared with T_h.
+// no candidate at level h. The rare flagged pairs go to a list that a
+// second kernel (k_harmsum_exact) sums exactly from P, in the same order,
+// and compares with T_h.
 __host__ __device__ constexpr int frac_order(int i) {
   return i == 0 ? 16 : i == 1 ? 8 : i == 2 ? 4 : i == 3 ? 12 : i < 8 ? 2 + 4 * (i - 4)
                                                                      : 1 + 2 * (i - 8);
