@@ -246,6 +246,83 @@ FDAS_DEV void dft2_brev(c2 (&x)[R]) {
   }
 }
 
+// v * exp(DIR 2 pi i e / 16) for 0 <= e < 16 (e a constant after
+// unrolling): quarter turns are swaps, eighth turns (|cos| = |sin|) take two
+// adds and two multiplies, the rest two multiplies and two fused
+// multiply-adds with the sine's negative as a constant.
+template <int DIR>
+FDAS_DEV c2 c2_tw16(c2 v, int e) {
+  e &= 15;
+  if (e == 0) return v;
+  if (e == 4) return DIR > 0 ? c2{p_neg(v.im), v.re} : c2{v.im, p_neg(v.re)};
+  if (e == 8) return c2{p_neg(v.re), p_neg(v.im)};
+  if (e == 12) return DIR > 0 ? c2{v.im, p_neg(v.re)} : c2{p_neg(v.im), v.re};
+  const int k = 2 * e;  // in 32nds of a turn
+  float c = kCos32[k & 15], sn = kSin32[k & 15];
+  if (k >= 16) {
+    c = -c;
+    sn = -sn;
+  }
+  if (DIR < 0) sn = -sn;
+  const float2 C = make_float2(c, c);
+  if (c == sn) return c2{p_mul(p_sub(v.re, v.im), C), p_mul(p_add(v.re, v.im), C)};
+  if (c == -sn) return c2{p_mul(p_add(v.re, v.im), C), p_mul(p_sub(v.im, v.re), C)};
+  return c2{p_fma(v.re, C, p_mul(v.im, make_float2(-sn, -sn))),
+            p_fma(v.re, make_float2(sn, sn), p_mul(v.im, C))};
+}
+
+// In-place 4-point DFT of two independent lanes, a_n -> X_k (natural
+// order), X_k = sum_n a_n exp(DIR 2 pi i n k / 4); the factor DIR i of the
+// odd outputs is folded into the adds.
+template <int DIR>
+FDAS_DEV void dft4_pairs(c2& a0, c2& a1, c2& a2, c2& a3) {
+  const c2 t0 = c2_add(a0, a2), t1 = c2_sub(a0, a2), t2 = c2_add(a1, a3), t3 = c2_sub(a1, a3);
+  a0 = c2_add(t0, t2);
+  a2 = c2_sub(t0, t2);
+  if (DIR > 0) {  // X1 = t1 + i t3, X3 = t1 - i t3
+    a1 = c2{p_sub(t1.re, t3.im), p_add(t1.im, t3.re)};
+    a3 = c2{p_add(t1.re, t3.im), p_sub(t1.im, t3.re)};
+  } else {        // X1 = t1 - i t3, X3 = t1 + i t3
+    a1 = c2{p_add(t1.re, t3.im), p_sub(t1.im, t3.re)};
+    a3 = c2{p_sub(t1.re, t3.im), p_add(t1.im, t3.re)};
+  }
+}
+
+// 16-point DFT of two independent lanes as 4 x 4 (decimation in frequency:
+// 4-point DFTs over n2 of x[n1 + 4 n2], twiddles exp(DIR 2 pi i n1 k1 / 16),
+// 4-point DFTs over n1); output k sits in x[brev<16>(k)], as with
+// dft2_brev<16, DIR>.
+template <int DIR>
+FDAS_DEV void dft16_pairs(c2 (&x)[16]) {
+  c2 y[16];  // y[n1 + 4 k1]
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) {
+    c2 a0 = x[n1], a1 = x[n1 + 4], a2 = x[n1 + 8], a3 = x[n1 + 12];
+    dft4_pairs<DIR>(a0, a1, a2, a3);
+    y[n1] = a0;
+    y[n1 + 4] = c2_tw16<DIR>(a1, n1);
+    y[n1 + 8] = c2_tw16<DIR>(a2, 2 * n1);
+    y[n1 + 12] = c2_tw16<DIR>(a3, 3 * n1);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    c2 a0 = y[4 * k1], a1 = y[4 * k1 + 1], a2 = y[4 * k1 + 2], a3 = y[4 * k1 + 3];
+    dft4_pairs<DIR>(a0, a1, a2, a3);
+    x[brev<16>(k1)] = a0;
+    x[brev<16>(k1 + 4)] = a1;
+    x[brev<16>(k1 + 8)] = a2;
+    x[brev<16>(k1 + 12)] = a3;
+  }
+}
+
+// the in-register DFT of R pairs used by the correlation (same output order
+// as dft2_brev<R, DIR>)
+template <int R, int DIR>
+FDAS_DEV void dft_pairs(c2 (&x)[R]) {
+  if constexpr (R == 16) dft16_pairs<DIR>(x);
+  else dft2_brev<R, DIR>(x);
+}
+
 // Radix-32 DFT over index e = 2 p + lane held as 16 pairs (p = 0..15,
 // lane 0 = even e, lane 1 = odd e). The first four radix-2 stages pair an
 // element with another of equal parity, so they run packed; the last stage
@@ -297,7 +374,7 @@ FDAS_DEV void cp_async_wait() {
 // f(n, value) receives output n in natural order; x is overwritten.
 template <int DIR, typename F>
 FDAS_DEV void dft32_dit(c2 (&x)[16], F&& f) {
-  dft2_brev<16, DIR>(x);
+  dft16_pairs<DIR>(x);
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
     const c2 v = x[brev<16>(k)];

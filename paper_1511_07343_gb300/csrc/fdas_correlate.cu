@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
         v[q * 4 + i] = c2_mul(v[q * 4 + i], c2{make_float2(f[4 * i], f[4 * i + 1]),
                                               make_float2(f[4 * i + 2], f[4 * i + 3])});
     }
-    dft2_brev<16, kInv>(v);
+    dft_pairs<16, kInv>(v);
 #pragma unroll
     for (int c = 1; c < 16; ++c) {
       const float4 tw = twA[a1 * 17 + c];
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
     // (no barrier: each thread writes its results into the slots it read)
 #pragma unroll
     for (int i = 0; i < NB2; ++i) {
-      dft2_brev<RA2, kInv>(w[i]);
+      dft_pairs<RA2, kInv>(w[i]);
       const int g = tid + T * i;
       const int u = g & 15, c = g >> 4;
 #pragma unroll
