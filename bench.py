@@ -43,8 +43,8 @@ FP32_LANES_PER_SM = 128
 # capture (profiles/dram_traffic_cfg2_n2e23_z200.md), each valid only for the
 # kernel source it was taken with (sha256 prefix of the file).
 MEASURED_TRAFFIC = {
-    "k_correlate_fused": (4.46e+09, "paper_1511_07343_gb300/csrc/fdas_correlate.cu", "9777a746c058d17e"),
-    "k_harmsum_staged": (8.475e+08, "paper_1511_07343_gb300/csrc/fdas_harmsum.cu", "ce8af2b859c9fa8e"),
+    "k_correlate_fused": (4.408e+09, "paper_1511_07343_gb300/csrc/fdas_correlate.cu", "ea53cf3cd8a00fbc"),
+    "k_harmsum_staged": (8.473e+08, "paper_1511_07343_gb300/csrc/fdas_harmsum.cu", "35745edd7841abeb"),
 }
 
 
