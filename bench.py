@@ -579,7 +579,7 @@ def main():
     # end to end through the C ABI with host buffers: K page-locked host
     # series in one fdas_search_host call (the library overlaps each trial's
     # copies with the previous trial's kernels), candidates sorted on the host
-    e2e_steps = 0 if args.no_e2e else (args.e2e_steps or 16)
+    e2e_steps = 0 if args.no_e2e else (args.e2e_steps or 32)
     h_series = torch.from_numpy(series[0]).pin_memory()
     h_out = np.zeros(max(e2e_steps, 1) * max_cands, dtype=fdas.CAND_DTYPE)
     h_cnt = np.zeros(max(e2e_steps, 1), dtype=np.int64)

@@ -107,10 +107,12 @@ int fdas_search(fdas_plan* plan, const float* d_series, int32_t n_trials,
  * kernels: series t+1 is copied in (on a copy stream of the plan, into a
  * second staging buffer) and trial t-1's candidates are read back and
  * sorted while trial t runs; page-locked host memory is needed for the
- * copies to overlap. The second staging buffer and candidate list are the
- * second trial lane's (below); where no lane is used (tensor-core or
- * half-bin modes) the first such call allocates them (4N + 16 max_cands
- * bytes). */
+ * copies to overlap. With the second trial lane (below) the series go
+ * through four staging buffers (the plan's, the lane's and two allocated on
+ * the first such call, 8N bytes), so the copy of trial t+1 never waits for
+ * a running trial; where no lane is used (tensor-core or half-bin modes)
+ * the first such call allocates a second staging buffer and candidate list
+ * (4N + 16 max_cands bytes). */
 int fdas_search_host(fdas_plan* plan, const float* h_series, int32_t n_trials,
                      fdas_cand* h_out, int64_t* h_counts);
 

@@ -84,12 +84,14 @@ void free_lane(fdas_plan* p);
 void free_plan(fdas_plan* p) {
   if (!p) return;
   free_lane(p);
-  for (int b = 0; b < 2; ++b) {
-    if (p->ev_in[b]) cudaEventDestroy(p->ev_in[b]);
-    if (p->ev_done[b]) cudaEventDestroy(p->ev_done[b]);
+  for (int k = 0; k < 4; ++k) {
+    if (p->ev_in[k]) cudaEventDestroy(p->ev_in[k]);
+    if (p->ev_done[k]) cudaEventDestroy(p->ev_done[k]);
   }
   if (p->cstream) cudaStreamDestroy(p->cstream);
   if (p->series2) cudaFree(p->series2);
+  for (float* b : p->series3)
+    if (b) cudaFree(b);
   if (p->cands2) cudaFree(p->cands2);
   if (p->count2) cudaFree(p->count2);
   void* ptrs[] = {p->tw_L, p->tw_M1, p->tw_M2, p->tw4_lo, p->tw4_hi, p->twN_lo, p->twN_hi,
@@ -280,7 +282,8 @@ int ensure_lane(fdas_plan* p) {
   l->cands = own.cands; l->count = own.count; l->hs_list = own.hs_list;
   l->hs_nlist = own.hs_nlist; l->stream = own.stream; l->device_bytes = own.device_bytes;
   l->series2 = nullptr; l->cands2 = nullptr; l->count2 = nullptr; l->cstream = nullptr;
-  l->ev_in[0] = l->ev_in[1] = l->ev_done[0] = l->ev_done[1] = nullptr;
+  l->series3[0] = l->series3[1] = nullptr;
+  for (int k = 0; k < 4; ++k) l->ev_in[k] = l->ev_done[k] = nullptr;
   l->lane = nullptr; l->ev_fork = l->ev_join = nullptr;
   l->dkeys = nullptr; l->dvals = nullptr; l->dbits = 0;
   return FDAS_OK;
@@ -329,10 +332,10 @@ int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_ca
     if ((rc = cuda_check(cudaStreamCreateWithFlags(&p->cstream, cudaStreamNonBlocking),
                          "copy stream")))
       return rc;
-    for (int b = 0; b < 2 && !rc; ++b) {
-      rc = cuda_check(cudaEventCreateWithFlags(&p->ev_in[b], cudaEventDisableTiming), "event");
+    for (int k = 0; k < 4 && !rc; ++k) {
+      rc = cuda_check(cudaEventCreateWithFlags(&p->ev_in[k], cudaEventDisableTiming), "event");
       if (!rc)
-        rc = cuda_check(cudaEventCreateWithFlags(&p->ev_done[b], cudaEventDisableTiming), "event");
+        rc = cuda_check(cudaEventCreateWithFlags(&p->ev_done[k], cudaEventDisableTiming), "event");
     }
     if (rc) return rc;
   }
@@ -348,10 +351,17 @@ int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_ca
     if (!p->cands2 && (rc = dalloc(p, &p->cands2, (size_t)p->max_cands))) return rc;
     if (!p->count2 && (rc = dalloc(p, &p->count2, 1))) return rc;
   }
-  float* buf[2] = {p->series, q[1] != p ? q[1]->series : p->series2};
-  fdas_cand* cbuf[2] = {p->cands, q[1] != p ? q[1]->cands : p->cands2};
-  unsigned long long* nbuf[2] = {p->count, q[1] != p ? q[1]->count : p->count2};
-  if (q[1] != p) {  // the lane starts after the caller's work on the plan stream
+  const bool lanes = q[1] != p;
+  // staging slots: with two lanes, 4, so that the copy of trial t + 1 waits
+  // for trial t - 3 (long done) rather than for trial t - 1 of its lane
+  const int K = lanes ? 4 : 2;
+  if (lanes && !d_series)
+    for (int e = 0; e < 2; ++e)
+      if (!p->series3[e] && (rc = dalloc(p, &p->series3[e], (size_t)p->N))) return rc;
+  float* buf[4] = {p->series, lanes ? q[1]->series : p->series2, p->series3[0], p->series3[1]};
+  fdas_cand* cbuf[2] = {p->cands, lanes ? q[1]->cands : p->cands2};
+  unsigned long long* nbuf[2] = {p->count, lanes ? q[1]->count : p->count2};
+  if (lanes) {  // the lane starts after the caller's work on the plan stream
     rc = cuda_check(cudaEventRecord(p->ev_fork, p->stream), "event");
     if (!rc) rc = cuda_check(cudaStreamWaitEvent(q[1]->stream, p->ev_fork, 0), "wait");
     if (rc) return rc;
@@ -361,7 +371,7 @@ int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_ca
   // read back and sort trial t (its kernels are done once ev_done fires)
   auto finish = [&](int32_t t) -> int {
     const int b = t & 1;
-    int r = cuda_check(cudaEventSynchronize(p->ev_done[b]), "trial done");
+    int r = cuda_check(cudaEventSynchronize(p->ev_done[t % K]), "trial done");
     unsigned long long cnt = 0;
     if (!r)
       r = cuda_check(cudaMemcpyAsync(&cnt, nbuf[b], sizeof(cnt), cudaMemcpyDeviceToHost, p->cstream),
@@ -388,31 +398,32 @@ int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_ca
     if (!rc) rc = cuda_check(cudaEventRecord(p->ev_in[0], p->cstream), "event");
   }
   for (int32_t t = 0; t < n_trials && !rc; ++t) {
-    const int b = t & 1, o = b ^ 1;
+    const int b = t & 1, k = t % K;
     if (d_series) {
       rc = run_trial(q[b], d_series + (size_t)t * p->N, cbuf[b], nbuf[b]);
-      if (!rc) rc = cuda_check(cudaEventRecord(p->ev_done[b], q[b]->stream), "event");
+      if (!rc) rc = cuda_check(cudaEventRecord(p->ev_done[k], q[b]->stream), "event");
       if (!rc && t >= 1) rc = finish(t - 1);
       continue;
     }
     if (t + 1 < n_trials) {
-      // staging buffer o was last read by trial t-1
-      if (t >= 1) rc = cuda_check(cudaStreamWaitEvent(p->cstream, p->ev_done[o], 0), "wait");
+      // staging slot k1 was last read by trial t + 1 - K
+      const int k1 = (t + 1) % K;
+      if (t + 1 >= K) rc = cuda_check(cudaStreamWaitEvent(p->cstream, p->ev_done[k1], 0), "wait");
       if (!rc)
-        rc = cuda_check(cudaMemcpyAsync(buf[o], h_series + (size_t)(t + 1) * p->N, bytes,
+        rc = cuda_check(cudaMemcpyAsync(buf[k1], h_series + (size_t)(t + 1) * p->N, bytes,
                                         cudaMemcpyHostToDevice, p->cstream),
                         "copy series");
-      if (!rc) rc = cuda_check(cudaEventRecord(p->ev_in[o], p->cstream), "event");
+      if (!rc) rc = cuda_check(cudaEventRecord(p->ev_in[k1], p->cstream), "event");
     }
-    if (!rc) rc = cuda_check(cudaStreamWaitEvent(q[b]->stream, p->ev_in[b], 0), "wait");
-    if (!rc) rc = run_trial(q[b], buf[b], cbuf[b], nbuf[b]);
-    if (!rc) rc = cuda_check(cudaEventRecord(p->ev_done[b], q[b]->stream), "event");
+    if (!rc) rc = cuda_check(cudaStreamWaitEvent(q[b]->stream, p->ev_in[k], 0), "wait");
+    if (!rc) rc = run_trial(q[b], buf[k], cbuf[b], nbuf[b]);
+    if (!rc) rc = cuda_check(cudaEventRecord(p->ev_done[k], q[b]->stream), "event");
     // the host reads back trial t-1 while trial t runs; trial t+1 reuses
-    // its candidate buffer only after this returns
+    // its lane's candidate list only after this returns
     if (!rc && t >= 1) rc = finish(t - 1);
   }
   if (!rc && n_trials >= 1) rc = finish(n_trials - 1);
-  if (!rc && q[1] != p) {  // the plan stream continues after the lane's work
+  if (!rc && lanes) {  // the plan stream continues after the lane's work
     rc = cuda_check(cudaEventRecord(p->ev_join, q[1]->stream), "event");
     if (!rc) rc = cuda_check(cudaStreamWaitEvent(p->stream, p->ev_join, 0), "wait");
     p->last_on_lane = n_trials >= 2 && ((n_trials - 1) & 1);
@@ -421,7 +432,7 @@ int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_ca
   if (rc) {
     cudaStreamSynchronize(p->cstream);
     cudaStreamSynchronize(p->stream);
-    if (q[1] != p) cudaStreamSynchronize(q[1]->stream);
+    if (lanes) cudaStreamSynchronize(q[1]->stream);
     return rc;
   }
   return overflow ? set_error(FDAS_ERR_OVERFLOW, "candidate list overflow") : FDAS_OK;

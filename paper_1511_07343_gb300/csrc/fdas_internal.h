@@ -71,14 +71,18 @@ struct fdas_plan {
   uint16_t* gbank = nullptr;   // 16-bit left factor, pre-tiled (see fdas_gemm.cu)
   int* gstatus = nullptr;      // device status word of the bounded waits
 
-  // host-input pipeline (second staging buffer, candidate list and count,
-  // a copy stream and events; made on the first multi-trial host call)
+  // host-input pipeline (more staging buffers, a second candidate list and
+  // count, a copy stream and events; made on the first multi-trial host
+  // call): staging slot k holds the series of trials t = k mod 4 (with the
+  // trial lane; slots 0, 1 are the plan's and the lane's series buffers,
+  // 2, 3 series3[0..1]) or t = k mod 2 (without it; slot 1 is series2)
   float* series2 = nullptr;
+  float* series3[2] = {nullptr, nullptr};
   fdas_cand* cands2 = nullptr;
   unsigned long long* count2 = nullptr;
   cudaStream_t cstream = nullptr;
-  cudaEvent_t ev_in[2] = {nullptr, nullptr};    // series copy landed
-  cudaEvent_t ev_done[2] = {nullptr, nullptr};  // trial finished on the plan stream
+  cudaEvent_t ev_in[4] = {nullptr, nullptr, nullptr, nullptr};    // series copy landed in slot k
+  cudaEvent_t ev_done[4] = {nullptr, nullptr, nullptr, nullptr};  // the trial reading slot k finished
 
   // second trial lane of multi-trial calls: a plan that shares this plan's
   // read-only tables and owns its own per-trial workspaces and stream, so
