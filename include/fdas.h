@@ -302,6 +302,12 @@ enum fdas_whiten_mode {
  * running median but a different estimate, so candidate lists differ. */
 int fdas_plan_set_whitening(fdas_plan* plan, int32_t mode);
 
+/* Block size of the harmonic-sum screen (the stage after step 7 of Section
+ * 4): 32 threads (one warp per block, the default) or 256 (eight warps per
+ * block; fdas_batch_create_tuned times both). Candidate lists do not depend
+ * on it. Any other value returns FDAS_ERR_INVALID. */
+int fdas_plan_set_harmsum_block(fdas_plan* plan, int32_t threads);
+
 /* Real FFT of one series without a plan and without allocating device memory.
  * The paper has no counterpart; this exists for callers that must not
  * allocate device memory (for example a real-time loop with a fixed device

@@ -694,6 +694,14 @@ int fdas_plan_set_whitening(fdas_plan* p, int32_t mode) {
   return FDAS_OK;
 }
 
+int fdas_plan_set_harmsum_block(fdas_plan* p, int32_t threads) {
+  if (!p) return set_error(FDAS_ERR_INVALID, "NULL plan");
+  if (threads != 32 && threads != 256)
+    return set_error(FDAS_ERR_INVALID, "harmonic-sum block must be 32 or 256 threads");
+  p->hs_threads = threads;
+  return FDAS_OK;
+}
+
 int fdas_plan_set_correlation(fdas_plan* p, int32_t mode) {
   if (!p) return set_error(FDAS_ERR_INVALID, "NULL plan");
   if (mode != FDAS_CORR_FFT && mode != FDAS_CORR_GEMM_BF16 && mode != FDAS_CORR_GEMM_FP16)

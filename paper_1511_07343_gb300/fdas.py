@@ -91,6 +91,7 @@ _SIGS = {
     "fdas_spectrum_noalloc": [_P, _I64, _P, _P],
     "fdas_plan_set_correlation": [_P, _I32],
     "fdas_plan_set_whitening": [_P, _I32],
+    "fdas_plan_set_harmsum_block": [_P, _I32],
     "fdas_plan_set_interbin": [_P, _I32],
     "fdas_distill": [_P, _P, _P, _P, _P],
     "fdas_batch_create_tuned": [ctypes.POINTER(_P), _I64, _I32, _I32, _I32, _I32,
@@ -271,6 +272,10 @@ def fdas_plan_set_interbin(plan, enable):
 
 def fdas_plan_set_whitening(plan, mode):
     _check(load().fdas_plan_set_whitening(plan, mode), "fdas_plan_set_whitening")
+
+
+def fdas_plan_set_harmsum_block(plan, threads):
+    _check(load().fdas_plan_set_harmsum_block(plan, threads), "fdas_plan_set_harmsum_block")
 
 
 def fdas_plan_set_correlation(plan, mode):

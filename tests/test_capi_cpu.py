@@ -105,6 +105,7 @@ def test_newer_entry_points_reject_null_and_bad_arguments(lib):
     INV = lib.FDAS_ERR_INVALID
     assert so.fdas_plan_set_correlation(None, 1) == INV
     assert so.fdas_plan_set_whitening(None, 1) == INV
+    assert so.fdas_plan_set_harmsum_block(None, 32) == INV
     assert so.fdas_plan_set_interbin(None, 1) == INV
     assert so.fdas_distill(None, None, None, None, None) == INV
     assert so.fdas_batch_set_graphs(None, 1) == INV

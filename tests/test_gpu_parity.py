@@ -170,9 +170,11 @@ def test_plane_matches_oracle(gpu_lib, N, zmax, m, L):
 
 
 # ----------------------------------------------------------- harmonic sums --
-def test_harmonic_sum_on_integer_plane_is_exact(gpu_lib):
+@pytest.mark.parametrize("block", [32, 256])
+def test_harmonic_sum_on_integer_plane_is_exact(gpu_lib, block):
     """Small integer powers make every float32 sum exact, so the GPU list
-    must equal the oracle's list exactly (no threshold band needed)."""
+    must equal the oracle's list exactly (no threshold band needed), with
+    either harmonic-sum block size."""
     fd = gpu_lib
     N, zmax, dz = 1 << 13, 40, 2
     Z, nb = 41, N // 2
@@ -181,6 +183,9 @@ def test_harmonic_sum_on_integer_plane_is_exact(gpu_lib):
     P[rng.integers(0, Z, 50), rng.integers(0, nb, 50)] = 25.0
     plan = make_plan(fd, N, zmax, dz, 64, 2048, 16, max_cands=1 << 22)
     try:
+        fd.fdas_plan_set_harmsum_block(plan, block)
+        with pytest.raises(fd.FdasError):
+            fd.fdas_plan_set_harmsum_block(plan, 128)
         info = fd.fdas_plan_get_info(plan)
         d_p = torch.from_numpy(P.astype(np.float32).ravel()).to(DEV)
         d_out = torch.empty(info.max_cands * 4, dtype=torch.int32, device=DEV)
@@ -203,7 +208,8 @@ def test_harmonic_sum_on_integer_plane_is_exact(gpu_lib):
         assert got[(c[0], c[1], c[2])] == c[3]
 
 
-def test_harmonic_sum_with_more_flags_than_the_list_holds(gpu_lib):
+@pytest.mark.parametrize("block", [32, 256])
+def test_harmonic_sum_with_more_flags_than_the_list_holds(gpu_lib, block):
     """A plane of powers 3..5 flags every bin pair at h = 16 (1.34 million
     pairs, more than the screen's list of 2^20 entries), so the list kernel
     sums the first 2^20 and the screen the rest inline; integer powers keep
@@ -215,6 +221,7 @@ def test_harmonic_sum_with_more_flags_than_the_list_holds(gpu_lib):
     P = rng.integers(3, 6, size=(Z, nb)).astype(np.float64)
     plan = make_plan(fd, N, zmax, dz, 64, 2048, 16, max_cands=1 << 23)
     try:
+        fd.fdas_plan_set_harmsum_block(plan, block)
         info = fd.fdas_plan_get_info(plan)
         d_p = torch.from_numpy(P.astype(np.float32).ravel()).to(DEV)
         d_out = torch.empty(info.max_cands * 4, dtype=torch.int32, device=DEV)
