@@ -94,7 +94,8 @@ FDAS_DEV void dft(float2 (&x)[R]) {
 // Radix used by stage s of a length-L Stockham FFT: 16 while at least 16
 // remains, then the leftover factor (2, 4 or 8).
 __host__ __device__ constexpr int stage_radix(int L, int ns) {
-  return (L / ns) >= 16 ? 16 : (L / ns);
+  // radix 16 while more than 32 points remain; a final 32 is one stage
+  return (L / ns) == 32 ? 32 : (L / ns) >= 16 ? 16 : (L / ns);
 }
 
 // One Stockham radix-R stage on NB transforms of length L stored back to
