@@ -367,7 +367,7 @@ int hs_launch(fdas_plan* p, const float* d_plane, const float* d_q4, fdas_cand* 
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return cuda_check(e, "SM count");
-  k_harmsum_exact<NLEV><<<4 * sms, 256, 0, p->stream>>>(d_plane, p->hs_list, p->hs_nlist,
+  k_harmsum_exact<NLEV><<<16 * sms, 256, 0, p->stream>>>(d_plane, p->hs_list, p->hs_nlist,
                                                         kHsListCap, w, p->Z, thresholds_of(p),
                                                         d_out, d_count, p->max_cands);
   return cuda_check(cudaGetLastError(), "k_harmsum_exact");
