@@ -37,11 +37,10 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "cfg2_n2e23_z200"
 METRIC = "DM trials/s at N=2^23 zmax=200"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) per launch at the benchmark size from one ncu
-# capture (profiles/dram_traffic_cfg2_n2e23_z200.md), each valid only for the
-# kernel source it was taken with (sha256 prefix of the file).
+# DRAM bytes (read + write) per launch at the benchmark size, from an ncu
+# counter capture of the kernel, each valid only for the kernel source it was
+# taken with (sha256 prefix of the file); None once that source changes.
 MEASURED_TRAFFIC = {
     "k_correlate_fused": (4.408e+09, "paper_1511_07343_gb300/csrc/fdas_correlate.cu", "ea53cf3cd8a00fbc"),
     "k_harmsum_staged": (8.473e+08, "paper_1511_07343_gb300/csrc/fdas_harmsum.cu", "35745edd7841abeb"),
@@ -74,7 +73,9 @@ class ClockSampler:
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+              "timestamp")
+    PERIOD_MS = 20
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
@@ -86,11 +87,23 @@ class ClockSampler:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                 stdout=self.file, stderr=subprocess.DEVNULL)
+            # wait (at most 5 s) for the first sample, so that sampling covers
+            # the timed region that follows
+            t_end = time.time() + 5.0
+            while time.time() < t_end and os.path.getsize(self.file.name) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
+        self.window = [None, None]
         return self
+
+    def mark_start(self):
+        self.window[0] = time.time()
+
+    def mark_end(self):
+        self.window[1] = time.time()
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -104,13 +117,28 @@ class ClockSampler:
         if self.proc is None or self.file is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.file.flush()
+        import datetime
         rows = []
         with open(self.file.name) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
+                if len(parts) >= 10:
                     rows.append(parts)
         os.unlink(self.file.name)
+        # samples inside the timed region (wall clock; one sample period of
+        # slack on each side); all samples if none fell inside
+        t0, t1 = self.window
+        inside = []
+        for r in rows:
+            try:
+                ts = datetime.datetime.strptime(r[9], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            if t0 is not None and t1 is not None and \
+                    t0 - self.PERIOD_MS / 1e3 <= ts <= t1 + self.PERIOD_MS / 1e3:
+                inside.append(r)
+        timed = bool(inside)
+        rows = inside or rows
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -123,7 +151,7 @@ class ClockSampler:
         power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows),
+                "reasons": reasons, "samples": len(rows), "samples_in_timed_region": timed,
                 "power_w_max": max(power) if power else None}
 
 
@@ -182,7 +210,26 @@ def plain_fp32_path(fdas, plan, info, p, dev, stream):
             plane.copy_(pw.view(Z, S * V)[:, :nb])
             fdas.fdas_stage_harmsum(plan, plane, cands, count)
         return count
+    step.cands = cands
     return step
+
+
+def candidate_agreement(a, b, thresholds):
+    """Key sets (r, z, h) of two candidate lists of the same series: common
+    keys, keys only in one of them, and how many of the latter lie outside
+    the 1e-4 T_h band around the threshold (judged by the power the list that
+    has the key reports)."""
+    def table(c):
+        return {(int(x["r_top"]), int(x["z_idx"]), int(x["h"])): float(x["power"]) for x in c}
+    ta, tb = table(a), table(b)
+    lvl = {1 << i: float(thresholds[i]) for i in range(5)}
+
+    def outside(keys, t):
+        return sum(1 for k in keys if abs(t[k] - lvl[k[2]]) > 1e-4 * lvl[k[2]])
+    only_a, only_b = set(ta) - set(tb), set(tb) - set(ta)
+    return {"common": len(set(ta) & set(tb)), "only_fused": len(only_a),
+            "only_plain": len(only_b), "only_fused_outside_band": outside(only_a, ta),
+            "only_plain_outside_band": outside(only_b, tb)}
 
 
 # ---------------------------------------------------------------------------
@@ -190,7 +237,7 @@ def plain_fp32_path(fdas, plan, info, p, dev, stream):
 # ten at an uneven length from [2^21, 2^22] (snapped to 2^a 3^b 5^c), the rest
 # 2^23 samples; continuous batching over device-resident plans.
 # ---------------------------------------------------------------------------
-def serve_measure(dev, n_sat=48, n_poisson=60, rate=11.32, seed=5):
+def serve_measure(dev, n_sat=48, n_poisson=600, rate=11.32, seed=5, slots=2, max_batch=2):
     import torch
     from paper_1511_07343_gb300.serve import Server
     from synthetic import make_series, random_chirps, snap_235
@@ -203,10 +250,10 @@ def serve_measure(dev, n_sat=48, n_poisson=60, rate=11.32, seed=5):
         chirps = random_chirps(rng, int(rng.integers(0, 4)), n, 200.0)
         pool.append(make_series(n, 5000 + i, chirps, device=dev))
     zs = [50, 100, 200]
-    with Server(n_max=1 << 23, n_slots=2, nharm=16, max_cands=1 << 20,
-                device=dev.index or 0) as srv:
-        # build every slot's plans once (device-resident afterwards)
-        warm = [srv.submit(pool[0], z) for z in zs for _ in range(2)]
+    with Server(n_max=1 << 23, n_slots=slots, nharm=16, max_cands=1 << 20,
+                device=dev.index or 0, max_batch=max_batch) as srv:
+        # every class and length once through every slot (first-use geometry)
+        warm = [srv.submit(pool[i], z) for z in zs for i in (0, 7) for _ in range(slots)]
         for f in warm:
             f.result()
         torch.cuda.synchronize(dev)
@@ -225,14 +272,22 @@ def serve_measure(dev, n_sat=48, n_poisson=60, rate=11.32, seed=5):
         poi = [f.result() for f in futs]
         t_poi = time.perf_counter() - t0
         stats = dict(srv.stats)
+        slot_gb = srv.slot_bytes / 1e9
     lat = percentiles([r.latency_ms for r in poi])
-    return {"slots": 2, "zmax_classes": zs,
+    by_class = {z: percentiles([r.latency_ms for r in poi if r.zmax == z]) for z in zs}
+    return {"slots": stats["slots"], "max_batch": max_batch, "zmax_classes": zs,
+            "slot_footprint_gb": slot_gb,
             "saturating": {"trials": n_sat, "trials_per_s": n_sat / t_sat,
-                           "latency_ms": percentiles([r.latency_ms for r in sat])},
+                           "latency_ms": percentiles([r.latency_ms for r in sat]),
+                           "mean_batch": float(np.mean([r.batch for r in sat]))},
             "poisson": {"rate_per_s": rate, "trials": n_poisson,
-                        "sustained_trials_per_s": n_poisson / t_poi, "latency_ms": lat},
+                        "sustained_trials_per_s": n_poisson / t_poi, "latency_ms": lat,
+                        "latency_ms_by_zmax": by_class,
+                        "trials_in_batches_of_2": sum(r.batch == 2 for r in poi)},
             "real_time_budget_trials_per_s": 6000 / 530.0, "stats": stats,
-            "what": "host series in, sorted candidates out; arrival to result, wall clock"}
+            "what": "host series in, sorted candidates out; arrival to result, wall clock; "
+                    "each slot runs up to max_batch queued trials (mixed zmax and length) "
+                    "as one fdas_search_batch call"}
 
 
 # ---------------------------------------------------------------------------
@@ -373,42 +428,101 @@ def precision_variants(fdas, p, dev, stream, d_series, ref_plane, ref_keys, step
 
 
 # ---------------------------------------------------------------------------
-# CPU baseline: the FP64 oracle, timed on a bounded sample of one trial.
+# CPU baseline: the FP64 oracle as it stands, its plane rows spread over the
+# host cores by a process pool (spawn: no worker inherits a CUDA context).
 # ---------------------------------------------------------------------------
-def oracle_trial_estimate(x, p, rows=3, hs_width=1 << 15):
-    """Seconds per trial of the oracle, from a bounded sample: the spectrum
-    and whitening of the full series, `rows` of the 201 plane rows, and the
-    harmonic sums over `hs_width` of the 2^22 top bins (all 201 rows); the
-    per-row and per-bin costs are scaled to the whole trial."""
+_W = {}
+
+
+def _pool_init(xw_bytes, nb, m):
+    _W["Xw"] = np.frombuffer(xw_bytes, dtype=np.complex128, count=nb)
+    _W["m"] = m
+
+
+def _pool_row(z):
+    """One plane row of the oracle (template + zero-padded FFT correlation);
+    returns the seconds it took in the worker."""
     from oracle import fdas_oracle as O
+    t0 = time.perf_counter()
+    tau = O.template_fresnel(float(z), _W["m"])
+    O.correlate_row(_W["Xw"], tau)
+    return time.perf_counter() - t0
+
+
+def _pool_hs(args):
+    """The oracle's harmonic sums and threshold over a (Z, width) sub-plane
+    of unit exponentials (the whitened-noise plane's distribution)."""
+    from oracle import fdas_oracle as O
+    seed, Z, width, nharm, sigma = args
+    P = np.random.default_rng(seed).exponential(size=(Z, width))
+    H = O.harmonic_sums(P, nharm)
+    T = O.thresholds(nharm, sigma)
+    for h, v in H.items():
+        np.nonzero(v >= T[h])
+    return width
+
+
+def _oracle_pool(Xw, m, cores):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    return ctx.Pool(cores, initializer=_pool_init, initargs=(Xw.tobytes(), Xw.shape[0], m))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_trial_estimate(x, p, rows=32, hs_width=1 << 16, small=None):
+    """Trials/s of the oracle on this host's cores, from a bounded sample of
+    one trial of the workload: the spectrum and whitening of the full series
+    (one core), `rows` of the Z plane rows (one per task, on a pool of all
+    cores, wall clock), and the harmonic sums and threshold over `hs_width` of
+    the nb top bins (all Z rows); each part scaled to the whole trial. With
+    `small` = (series, params) the whole oracle search of that (small)
+    workload is also timed end to end."""
+    from oracle import fdas_oracle as O
+    cores = host_cores()
     t0 = time.perf_counter()
     Xw = O.whiten(O.spectrum(x))
     t_pre = time.perf_counter() - t0
     zs = O.z_values(p["zmax"], p["dz"])
     Z = len(zs)
-    t0 = time.perf_counter()
-    for z in zs[:: max(1, Z // rows)][:rows]:
-        tau = O.template_fresnel(float(z), p["m"])
-        O.correlate_row(Xw, tau)
-    t_row = (time.perf_counter() - t0) / rows
-    rng = np.random.default_rng(0)
-    Psub = rng.exponential(size=(Z, hs_width))
-    t0 = time.perf_counter()
-    H = O.harmonic_sums(Psub, p["nharm"])
-    T = O.thresholds(p["nharm"], p["sigma"])
-    for h, v in H.items():
-        np.nonzero(v >= T[h])
-    t_hs = (time.perf_counter() - t0) * (x.shape[0] // 2) / hs_width
-    total = t_pre + Z * t_row + t_hs
-    sample = (f"oracle on 1 host core: full spectrum+whitening, {rows} of {Z} plane rows, "
-              f"harmonic sums over {hs_width} of {x.shape[0] // 2} bins; scaled to one trial "
-              f"({os.cpu_count()} host cores present)")
-    return total, sample
+    pick = zs[:: max(1, Z // rows)][:rows]
+    with _oracle_pool(Xw, p["m"], cores) as pool:
+        pool.map(_pool_row, pick[:cores])          # workers up and warm
+        t0 = time.perf_counter()
+        pool.map(_pool_row, pick, chunksize=1)
+        t_rows = (time.perf_counter() - t0) * Z / len(pick)
+        t0 = time.perf_counter()
+        done = sum(pool.map(_pool_hs, [(i, Z, hs_width, p["nharm"], p["sigma"])
+                                       for i in range(cores)], chunksize=1))
+        t_hs = (time.perf_counter() - t0) * (x.shape[0] // 2) / done
+    total = t_pre + t_rows + t_hs
+    out = {"value": 1.0 / total, "unit": "trials/s", "cores": cores, "kind": "oracle",
+           "sample": (f"FP64 oracle on {cores} host cores: full spectrum+whitening (1 core, "
+                      f"{t_pre:.2f} s), {len(pick)} of {Z} plane rows on a {cores}-process pool "
+                      f"({t_rows * len(pick) / Z:.2f} s wall), harmonic sums over {cores} x {hs_width} of "
+                      f"{x.shape[0] // 2} bins x {Z} rows on the pool; rows and bins scaled to "
+                      f"one trial"),
+           "seconds_per_trial": total}
+    if small is not None:
+        xs, ps = small
+        t0 = time.perf_counter()
+        O.search(xs, ps["zmax"], ps["dz"], ps["m"], ps["nharm"], ps["sigma"])
+        out["small_workload"] = {"workload": "cfg1_n2e17_z50", "trials": 1,
+                                 "trials_per_s": 1.0 / (time.perf_counter() - t0),
+                                 "cores": 1, "what": "whole oracle search of the 2^17-sample, "
+                                                     "zmax = 50 trial, end to end"}
+    return out
 
 
 def run_reference(args):
-    """The oracle as the reference arm: each step is 1/Z of a trial (one
-    plane row, 1/Z of the harmonic sums and of the spectrum+whitening)."""
+    """The oracle as the reference arm, on a pool of all host cores: each
+    step is 1/Z of a trial (one plane row, 1/Z of the harmonic sums and of
+    the spectrum+whitening); steps run concurrently, one per core."""
     from oracle import fdas_oracle as O
     from synthetic import workload
     rank = int(os.environ.get("RANK", "0"))
@@ -424,23 +538,22 @@ def run_reference(args):
     width = max(1, (x.shape[0] // 2) // Z)
     Psub = rng.exponential(size=(Z, width))
     T = O.thresholds(p["nharm"], p["sigma"])
-
-    def step(i):
-        tau = O.template_fresnel(float(zs[i % Z]), p["m"])
-        O.correlate_row(Xw, tau)
-        H = O.harmonic_sums(Psub, p["nharm"])
-        for h, v in H.items():
-            np.nonzero(v >= T[h])
-
-    for i in range(args.warmup):
-        step(i)
     t0 = time.perf_counter()
-    for i in range(args.steps):
-        step(i)
-    dt = (time.perf_counter() - t0) / args.steps + t_pre
+    H = O.harmonic_sums(Psub, p["nharm"])
+    for h, v in H.items():
+        np.nonzero(v >= T[h])
+    t_hs = time.perf_counter() - t0           # 1/Z of the harmonic sums (one core)
+    cores = host_cores()
+    with _oracle_pool(Xw, p["m"], cores) as pool:
+        pool.map(_pool_row, [zs[i % Z] for i in range(args.warmup)], chunksize=1)
+        t0 = time.perf_counter()
+        pool.map(_pool_row, [zs[i % Z] for i in range(args.steps)], chunksize=1)
+        wall = time.perf_counter() - t0
+    dt = wall / args.steps + (t_pre + t_hs) / cores
     value = 1.0 / (Z * dt)
-    sample = (f"each step = 1/{Z} of a trial on 1 host core (one plane row, harmonic sums over "
-              f"{width} bins x {Z} rows, 1/{Z} of spectrum+whitening)")
+    sample = (f"each step = 1/{Z} of a trial (one plane row on one of {cores} pool processes, "
+              f"plus 1/{Z} of the spectrum+whitening and of the harmonic sums over all bins, "
+              f"timed on one core and shared over the {cores} cores)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "trials/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -448,8 +561,8 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "N": p["N"], "zmax": p["zmax"], "dz": p["dz"],
                        "templates": Z, "template_width": p["m"], "segment": p["L"],
                        "nharm": p["nharm"], "sigma": p["sigma"]},
-            "cpu_baseline": {"value": value, "unit": "trials/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "trials/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "trials/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -548,11 +661,13 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
+        clk.mark_start()
         evs[0].record(stream)
         for n in calls:
             trials(n)
         evs[1].record(stream)
         torch.cuda.synchronize(dev)
+        clk.mark_end()
         if world > 1:
             dist.barrier()
     ms = reduce_max(evs[0].elapsed_time(evs[-1]), world, dev)
@@ -614,9 +729,20 @@ def main():
         pe[1].record(stream)
         torch.cuda.synchronize(dev)
         pms = reduce_max(pe[0].elapsed_time(pe[1]), world, dev) / args.plain_steps
+        # candidate recovery of both paths on the same series
+        agree = []
+        for i in range(min(2, len(d_series))):
+            pcnt = pstep(d_series[i])
+            torch.cuda.synchronize(dev)
+            k = min(int(pcnt.item()), max_cands)
+            plain_c = pstep.cands[: k * 16].cpu().numpy().view(fdas.CAND_DTYPE)
+            fdas.fdas_search(plan, d_series[i], 1, h_out, h_cnt)
+            fused_c = h_out[: min(int(h_cnt[0]), max_cands)]
+            agree.append(candidate_agreement(fused_c, plain_c, info.thresholds))
         plain = {"value": world * 1e3 / pms, "unit": "trials/s", "ms_per_step": pms,
                  "steps": args.plain_steps, "speedup": value / (world * 1e3 / pms),
                  "candidates_last_step": int(pcnt.item()),
+                 "recovery": agree,
                  "what": "unfused FP32 path: cuFFT (torch.fft) real FFT, segment and inverse FFTs, "
                          "elementwise multiply into a materialised complex plane, power, edge trim; "
                          "this library's whitening and harmonic sum"}
@@ -685,15 +811,24 @@ def main():
     elif dom == "correlate":
         flops = S * Z * (5.0 * L * math.log2(L) + 6.0 * L + 3.0 * V)
         sm_max = peaks.get("sm_max_mhz", 2070.0)
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
         achieved = flops / (stage_ms[dom] / 1e3) / 1e12
+        # HBM view of the same launch: the plane and 4-bin maxima it writes,
+        # the segment spectra and template bank it reads (once each)
+        hbm_bytes = Z * nb * 4.0 + Z * (nb // 4) * 4.0 + S * L * 8.0 + Z * L * 8.0
+        hbm_ach = hbm_bytes / (stage_ms[dom] / 1e3) / 1e9
         roof = {"kernel": "k_correlate_fused", "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": measured_traffic("k_correlate_fused"),
-                "peak_source": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                               f"{sm_max:.0f} MHz",
+                "peak_source": f"FP32 FMA: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                               f"{sm_max:.0f} MHz (derived; {peak_kind} sm_max_mhz)",
                 "algorithmic": f"S*Z*(5 L log2 L + 6 L + 3 V) = {flops:.3e} flop per launch",
-                "hbm_view_gbs": (Z * nb * 4) / (stage_ms[dom] / 1e3) / 1e9}
+                "hbm": {"achieved": hbm_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": hbm_ach / peaks["hbm_gbs"], "bytes": hbm_bytes,
+                        "peak_source": f"{peak_kind} hbm_gbs",
+                        "algorithmic": "plane + 4-bin maxima written, segment spectra + "
+                                       "template bank read once"}}
     else:
         nbytes = Z * (nb // 4) * 4.0  # one read of the 4-bin maxima
         peak = peaks["hbm_gbs"]
@@ -743,9 +878,8 @@ def main():
     if rank == 0 and not args.no_serve and args.log2n is None:
         line["serving"] = serve_measure(dev)
     if rank == 0 and not args.no_cpu_baseline:
-        t_trial, sample = oracle_trial_estimate(series[0], p)
-        line["cpu_baseline"] = {"value": 1.0 / t_trial, "unit": "trials/s", "cores": 1,
-                                "kind": "oracle", "sample": sample}
+        line["cpu_baseline"] = oracle_trial_estimate(series[0], p,
+                                                     small=workload("cfg1_n2e17_z50"))
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:

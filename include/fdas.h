@@ -22,6 +22,13 @@
  *  - A plan is bound to the CUDA stream given at creation (NULL = the legacy
  *    default stream) and is not thread-safe; use one plan per stream.
  *  - Complex data are interleaved float32 (re, im) pairs, i.e. float2.
+ *  - Device pointers must be aligned for the vector accesses the kernels
+ *    make through them: series and spectra 8 bytes (float2), the whitening
+ *    stage's input and output and every plane 16 bytes (float4), 64-bit
+ *    counts 8 bytes, candidate and peak lists 4 bytes. Memory from
+ *    cudaMalloc (or a torch tensor's storage) is aligned; a view that starts
+ *    at an odd element may not be. A misaligned pointer returns
+ *    FDAS_ERR_INVALID before any device work.
  *
  * Notation: N samples per series, nb = N/2 Fourier bins (Nyquist dropped),
  * z_j = -zmax + j*dz for j = 0..Z-1 (Z = 2*zmax/dz + 1, z = fdot*T^2 in bins,
@@ -137,33 +144,50 @@ int fdas_search_device(fdas_plan* plan, const float* d_series, int32_t n_trials,
  * The first such call allocates the lane (counted in device_bytes); it is
  * remade if the plan's shape changes and freed with the plan. */
 
-/* Batches of DM trials of uneven length (series of different N).
+/* Batches of DM trials (Section 1: the search runs once per de-dispersed
+ * trial, about 6000 per 530 s observation for the SKA) of uneven length and
+ * mixed acceleration range, each trial through the whole path of Section 4
+ * (steps 2-7) plus the harmonic sum, threshold and compaction.
  * fdas_batch_create makes one plan for the longest series N_max (same
- * arguments and limits as fdas_plan_create) whose workspaces and templates
- * serve every trial; fdas_search_batch runs trial t of length N[t]
- * (N[t] <= N_max, N[t] = 2^a 3^b 5^c with a >= 12) from d_series[t] (host
- * array of device pointers, N[t] floats each) and, like fdas_search_device,
- * enqueues the whole path asynchronously with unsorted candidates at
- * d_out + t*max_cands and the exact count in d_counts[t] (device int64).
- * The real-FFT geometry of each new length is built (and cached) on first
- * use, which allocates its small twiddle tables. */
+ * arguments and limits as fdas_plan_create); its zmax, template width and
+ * segment length are the batch's first zmax class. fdas_batch_add_class adds
+ * another class (zmax, template_width, segment) under the same dz, nharm,
+ * sigma and max_cands (same limits as fdas_plan_create; one class per zmax):
+ * it makes that class's template bank (Section 4, initialisation) and grows
+ * the shared workspaces (plane, 4-bin maxima, segment spectra) to fit the
+ * largest class; every class uses the one set of per-trial workspaces, so a
+ * batch holds one plane of the largest class, not one per class. It
+ * synchronises the batch's stream; call it between searches.
+ * fdas_search_batch runs trial t of length N[t] (N[t] <= N_max,
+ * N[t] = 2^a 3^b 5^c with a >= 12) in the class of zmax[t] (host array; NULL
+ * = the first class for every trial) from d_series[t] (host array of device
+ * pointers, N[t] floats each) and, like fdas_search_device, enqueues the
+ * whole path asynchronously with unsorted candidates at d_out + t*max_cands
+ * and the exact count in d_counts[t] (device int64). A zmax with no class
+ * returns FDAS_ERR_INVALID before any device work. The real-FFT geometry of
+ * each new (length, class) pair is built (and cached) on first use, which
+ * allocates its small twiddle tables. */
 typedef struct fdas_batch fdas_batch;
 int fdas_batch_create(fdas_batch** out, int64_t N_max, int32_t zmax, int32_t dz,
                       int32_t template_width, int32_t segment, int32_t nharm, float sigma,
                       int64_t max_cands, void* stream);
+int fdas_batch_add_class(fdas_batch* batch, int32_t zmax, int32_t template_width,
+                         int32_t segment);
 int fdas_batch_destroy(fdas_batch* batch);
 int fdas_search_batch(fdas_batch* batch, const float* const* d_series, const int64_t* N,
-                      int32_t n_trials, fdas_cand* d_out, int64_t* d_counts);
+                      const int32_t* zmax, int32_t n_trials, fdas_cand* d_out,
+                      int64_t* d_counts);
 /* On a stream other than the legacy default stream, fdas_search_batch
  * captures the whole batch (every trial's kernels and count resets, in
  * order) into one CUDA graph and launches it as a single graph launch. The
  * executable graph is kept: a later call with the same series pointers,
- * lengths and output pointers replays it without capturing; other
+ * lengths, zmax values and output pointers replays it without capturing; other
  * arguments re-capture and update it in place when the topology allows.
  * fdas_batch_set_graphs(batch, 0) launches the kernels directly instead. */
 int fdas_batch_set_graphs(fdas_batch* batch, int32_t enable);
 
-/* Autotuned batch: times one trial of every combination of segment length
+/* Autotuned batch (first class only; classes added later keep the segment
+ * length they are given): times one trial of every combination of segment length
  * L in {2048, 4096, 8192} with L >= 2m and harmonic-sum block of 256 or 32
  * threads (16384 or 2048 top bins per block) on a probe series of N_max
  * samples (d_probe, device; NULL = seeded Gaussian white noise made on the
@@ -188,6 +212,8 @@ typedef struct {
   int32_t tuned_segment[8];  /* the configurations timed: L ... */
   int32_t tuned_hs_block[8]; /* ... harmonic-sum block ... */
   float tuned_ms[8];         /* ... and their median trial times (ms) */
+  int32_t n_classes;         /* zmax classes (1 + fdas_batch_add_class calls) */
+  int64_t device_bytes;      /* device memory the batch holds */
 } fdas_batch_info;
 int fdas_batch_get_info(const fdas_batch* batch, fdas_batch_info* info);
 
@@ -244,6 +270,20 @@ enum fdas_corr_mode {
  * A bounded device wait that gives up makes the next fdas_search return
  * FDAS_ERR_TIMEOUT. */
 int fdas_plan_set_correlation(fdas_plan* plan, int32_t mode);
+
+/* Test hook for the bounded device waits of the tensor-core correlation
+ * (the paper has no counterpart; this exercises the failure handling): every
+ * pipeline wait of k_gemm_correlate (bulk copies landing, MMA commits,
+ * hand-offs between its warp roles) gives up after `polls` polls of its
+ * mbarrier (0 = the default, 2^23 polls with back-off, about a second), after
+ * which every role leaves its loop and the next fdas_search (or
+ * fdas_stage_plane) returns FDAS_ERR_TIMEOUT and clears the status. Whatever
+ * the limit, the kernel then waits with the full default bound for the bulk
+ * copies it issued and the MMAs it committed (they complete on their own)
+ * and frees its tensor memory before it returns, so the context stays
+ * usable. polls = 1 makes the first wait run out; a test uses it to check
+ * the error path. No effect on the FFT correlation, which waits on nothing. */
+int fdas_plan_set_wait_limit(fdas_plan* plan, uint32_t polls);
 
 /* One distilled detection: a local maximum of the candidate list with its
  * Gaussian-equivalent significance. */
@@ -319,7 +359,9 @@ int fdas_plan_set_harmsum_block(fdas_plan* plan, int32_t threads);
  * Scratch: a fixed 8.5 MB array in device memory that every GPU loading this
  * library holds until the process exits; no call allocates or frees memory.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture. All
+ * device current); make that first call before any stream capture. The
+ * address is cached for the life of the process: after cudaDeviceReset on a
+ * device, do not call this entry point on that device again. All
  * calls share the one array: calls whose work overlaps on a GPU (different
  * streams or host threads) race and give wrong results; serialise them.
  * Every value the kernels read from the array is written earlier in the same

@@ -368,6 +368,56 @@ def distill(rows, Z: int):
     return out
 
 
+def correlate_band(Xw: np.ndarray, tau: np.ndarray, c0: int, c1: int) -> np.ndarray:
+    """A(r) = sum_{d=-m/2}^{m/2-1} Xw[r+d] tau(d) for r = c0 .. c1-1 only, Xw = 0
+    outside [0, nb): one zero-padded FFT correlation of the sub-band
+    Xw[c0 - m/2, c1 + m/2) (the same definition as correlate_row, restricted
+    to a column range, so that full-size checks need not form whole rows)."""
+    nb = Xw.shape[0]
+    m = tau.shape[0]
+    lo = c0 - m // 2
+    width = (c1 - c0) + m
+    band = np.zeros(width, dtype=np.complex128)
+    a, b = max(lo, 0), min(lo + width, nb)
+    if b > a:
+        band[a - lo: b - lo] = Xw[a:b]
+    # band[i] = Xw[lo + i]; A(c0 + t) = sum_d band[t + m/2 + d] tau(d)
+    full = correlate_row(band, tau)
+    return full[m // 2: m // 2 + (c1 - c0)]
+
+
+def subharmonic_fractions(nharm: int):
+    """The distinct ratios k/h (k = 1..h, h = 1, 2, 4..nharm) as (q, Q) with
+    k/h = q/Q, Q = nharm: round(k r / h) depends on k/h alone."""
+    return [(q, nharm) for q in range(1, nharm + 1)]
+
+
+def harmonic_sums_window(Xw: np.ndarray, taus: np.ndarray, nharm: int, r_a: int, r_b: int) -> dict:
+    """H_h[j, r - r_a] for every row j and the top bins r_a <= r < r_b, with
+    the plane formed only where these sums read it: for each ratio k/h the
+    columns round(k r / h), r in [r_a, r_b), of every row, by correlate_band.
+    Same definition and summation order (k = 1..h) as harmonic_sums."""
+    Z = taus.shape[0]
+    zc = (Z - 1) // 2
+    r = np.arange(r_a, r_b, dtype=np.int64)
+    j = np.arange(Z)
+    bands = {}
+    for q, Q in subharmonic_fractions(nharm):
+        cols = subharmonic_r(r, q, Q)
+        c0, c1 = int(cols.min()), int(cols.max()) + 1
+        rows = np.stack([np.abs(correlate_band(Xw, t, c0, c1)) ** 2 for t in taus])
+        bands[(q, Q)] = (c0, rows)
+    out = {}
+    for h in harmonic_levels(nharm):
+        H = np.zeros((Z, r_b - r_a))
+        for k in range(1, h + 1):
+            q, Q = k * nharm // h, nharm
+            c0, rows = bands[(q, Q)]
+            H += rows[np.ix_(subharmonic_j(j, k, h, zc), subharmonic_r(r, k, h) - c0)]
+        out[h] = H
+    return out
+
+
 def harmonic_sum_cells(Xw, taus, nharm: int, j_idx, r_idx) -> dict:
     """H_h at individual top cells from direct plane-cell sums (full-size checks)."""
     Z = taus.shape[0]

@@ -2,6 +2,7 @@
 
 The compute path lives in the CUDA library ``_build/libfdas_gb300.so``
 (sources in ``csrc/``, C ABI in ``include/fdas.h``); ``fdas`` is its ctypes
-binding and ``search`` a small convenience layer over it.
+binding (argument marshalling only) and ``serve`` a continuous-batching
+serving loop over it.
 """
 from . import fdas  # noqa: F401

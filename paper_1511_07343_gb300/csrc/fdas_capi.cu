@@ -235,9 +235,11 @@ void free_lane(fdas_plan* p) {
 }
 
 // The lane for the plan's current shape, made or remade as needed, with the
-// plan's shared fields copied in.
+// plan's shared fields copied in. Its plane, 4-bin maxima and segment buffers
+// have the plan's capacities (a batch with several zmax classes sizes those
+// for its largest class).
 int ensure_lane(fdas_plan* p) {
-  const int64_t key[5] = {p->N, p->Z, (int64_t)p->S * p->L, p->max_cands, plane_width(p)};
+  const int64_t key[5] = {p->N, p->plane_cap, p->seg_cap, p->max_cands, plane_width(p)};
   if (p->lane && !std::equal(key, key + 5, p->lane_key)) free_lane(p);
   if (!p->lane) {
     fdas_plan* l = new fdas_plan(*p);
@@ -253,9 +255,9 @@ int ensure_lane(fdas_plan* p) {
     if (!rc) rc = dalloc(l, &l->spec, (size_t)p->nb);
     if (!rc) rc = dalloc(l, &l->spec2, (size_t)p->M);
     if (!rc) rc = dalloc(l, &l->white, (size_t)p->nb);
-    if (!rc) rc = dalloc(l, &l->seg, (size_t)p->S * p->L);
-    if (!rc) rc = dalloc(l, &l->plane, (size_t)p->Z * plane_width(p));
-    if (!rc) rc = dalloc(l, &l->q4, (size_t)p->Z * plane_width(p) / 4);
+    if (!rc) rc = dalloc(l, &l->seg, (size_t)p->seg_cap);
+    if (!rc) rc = dalloc(l, &l->plane, (size_t)p->plane_cap);
+    if (!rc) rc = dalloc(l, &l->q4, (size_t)p->plane_cap / 4);
     if (!rc) rc = dalloc(l, &l->cands, (size_t)p->max_cands);
     if (!rc) rc = dalloc(l, &l->count, 1);
     if (!rc) rc = dalloc(l, &l->hs_list, (size_t)kHsListCap);
@@ -278,7 +280,8 @@ int ensure_lane(fdas_plan* p) {
   *l = *p;
   l->series = own.series; l->zbuf = own.zbuf; l->spec = own.spec; l->spec2 = own.spec2;
   l->white = own.white; l->seg = own.seg; l->plane = own.plane; l->q4 = own.q4;
-  l->plane_cap = (int64_t)p->Z * plane_width(p);
+  l->plane_cap = p->plane_cap;
+  l->seg_cap = p->seg_cap;
   l->cands = own.cands; l->count = own.count; l->hs_list = own.hs_list;
   l->hs_nlist = own.hs_nlist; l->stream = own.stream; l->device_bytes = own.device_bytes;
   l->series2 = nullptr; l->cands2 = nullptr; l->count2 = nullptr; l->cstream = nullptr;
@@ -502,6 +505,7 @@ int fdas_plan_create(fdas_plan** out, int64_t N, int32_t zmax, int32_t dz, int32
   TRY(dalloc(p, &p->spec2, (size_t)p->M));
   TRY(dalloc(p, &p->white, (size_t)p->nb));
   TRY(dalloc(p, &p->seg, (size_t)p->S * L));
+  p->seg_cap = (int64_t)p->S * L;
   TRY(dalloc(p, &p->plane, (size_t)p->Z * p->nb));
   TRY(dalloc(p, &p->q4, (size_t)p->Z * (p->nb / 4)));
   p->plane_cap = (int64_t)p->Z * p->nb;
@@ -555,6 +559,7 @@ int fdas_search(fdas_plan* p, const float* d_series, int32_t n_trials, fdas_cand
                 int64_t* h_counts) {
   if (!p || !d_series || n_trials < 0 || (n_trials > 0 && (!h_out || !h_counts)))
     return set_error(FDAS_ERR_INVALID, "bad argument to fdas_search");
+  if (int rc = check_aligned(d_series, 8, "d_series")) return rc;
   if (n_trials > 1 && p->stream != nullptr)  // read-back of trial t-1 overlaps trial t
     return host_pipeline(p, nullptr, n_trials, h_out, h_counts, d_series);
   return search_impl(p, d_series, n_trials, h_out, h_counts);
@@ -587,6 +592,9 @@ int fdas_search_device(fdas_plan* p, const float* d_series, int32_t n_trials, fd
                        int64_t* d_counts) {
   if (!p || !d_series || n_trials < 0 || (n_trials > 0 && (!d_out || !d_counts)))
     return set_error(FDAS_ERR_INVALID, "bad argument to fdas_search_device");
+  if (int rc = check_aligned(d_series, 8, "d_series")) return rc;
+  if (int rc = check_aligned(d_out, 4, "d_out")) return rc;
+  if (int rc = check_aligned(d_counts, 8, "d_counts")) return rc;
   fdas_plan* q[2] = {p, p};
   if (n_trials > 1 && lanes_usable(p)) {
     // odd trials on the second lane: it starts after the caller's work on
@@ -623,17 +631,23 @@ int fdas_plane_debug(fdas_plan* p, float* d_plane) {
 
 int fdas_stage_spectrum(fdas_plan* p, const float* d_series, float* d_spectrum) {
   if (!p || !d_series || !d_spectrum) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  if (int rc = check_aligned(d_series, 8, "d_series")) return rc;
+  if (int rc = check_aligned(d_spectrum, 8, "d_spectrum")) return rc;
   return launch_spectrum(p, d_series, reinterpret_cast<float2*>(d_spectrum));
 }
 
 int fdas_stage_whiten(fdas_plan* p, const float* d_spectrum, float* d_white) {
   if (!p || !d_spectrum || !d_white) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  if (int rc = check_aligned(d_spectrum, 16, "d_spectrum")) return rc;
+  if (int rc = check_aligned(d_white, 16, "d_white")) return rc;
   return launch_whiten(p, reinterpret_cast<const float2*>(d_spectrum),
                        reinterpret_cast<float2*>(d_white));
 }
 
 int fdas_stage_plane(fdas_plan* p, const float* d_white, float* d_plane) {
   if (!p || !d_white || !d_plane) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  if (int rc = check_aligned(d_white, 8, "d_white")) return rc;
+  if (int rc = check_aligned(d_plane, 16, "d_plane")) return rc;
   if (p->corr_mode != FDAS_CORR_FFT) {
     // the tensor-core kernel reads the plan's whitened spectrum
     int rc = cuda_check(cudaMemcpyAsync(p->white, d_white, sizeof(float2) * (size_t)p->nb,
@@ -651,6 +665,10 @@ int fdas_distill(fdas_plan* p, const fdas_cand* d_cands, const int64_t* d_count,
                  fdas_peak* d_peaks, int64_t* d_npeaks) {
   if (!p || !d_cands || !d_count || !d_peaks || !d_npeaks)
     return set_error(FDAS_ERR_INVALID, "NULL argument");
+  if (int rc = check_aligned(d_cands, 4, "d_cands")) return rc;
+  if (int rc = check_aligned(d_peaks, 4, "d_peaks")) return rc;
+  if (int rc = check_aligned(d_count, 8, "d_count")) return rc;
+  if (int rc = check_aligned(d_npeaks, 8, "d_npeaks")) return rc;
   return launch_distill(p, d_cands, d_count, d_peaks, d_npeaks);
 }
 
@@ -727,8 +745,17 @@ int fdas_plan_set_correlation(fdas_plan* p, int32_t mode) {
   return cuda_check(cudaStreamSynchronize(p->stream), "template matrix");
 }
 
+int fdas_plan_set_wait_limit(fdas_plan* p, uint32_t polls) {
+  if (!p) return set_error(FDAS_ERR_INVALID, "NULL plan");
+  p->gm_spin = polls;
+  return FDAS_OK;
+}
+
 int fdas_stage_harmsum(fdas_plan* p, const float* d_plane, fdas_cand* d_out, int64_t* d_count) {
   if (!p || !d_plane || !d_out || !d_count) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  if (int e = check_aligned(d_plane, 16, "d_plane")) return e;
+  if (int e = check_aligned(d_out, 4, "d_out")) return e;
+  if (int e = check_aligned(d_count, 8, "d_count")) return e;
   int rc = cuda_check(cudaMemsetAsync(d_count, 0, sizeof(int64_t), p->stream), "memset count");
   if (rc) return rc;
   auto* cnt = reinterpret_cast<unsigned long long*>(d_count);
@@ -745,11 +772,13 @@ int fdas_template_taps(fdas_plan* p, double* d_taps) {
 
 int fdas_template_bank(fdas_plan* p, float* d_bank) {
   if (!p || !d_bank) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  if (int rc = check_aligned(d_bank, 8, "d_bank")) return rc;
   return launch_bank_natural(p, reinterpret_cast<float2*>(d_bank));
 }
 
 int fdas_profile_trial(fdas_plan* p, const float* d_series, float* h_ms) {
   if (!p || !d_series || !h_ms) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  if (int rc = check_aligned(d_series, 8, "d_series")) return rc;
   cudaEvent_t ev[6];
   for (int i = 0; i < 6; ++i) {
     if (cudaEventCreate(&ev[i]) != cudaSuccess) {
@@ -791,20 +820,27 @@ int fdas_host_fresnel(double x, double* C, double* S) {
 }
 
 // ---------------------------------------------------------------------------
-// Batches of DM trials of uneven length: one plan's workspaces (sized for the
-// longest series) serve every trial; per length only the real-FFT geometry
-// and its twiddle tables differ, cached as lightweight views of the plan.
+// Batches of DM trials (Section 1: the search runs once per de-dispersed
+// trial, ~6000 per observation) of uneven length and mixed acceleration
+// range. One plan's per-trial workspaces, sized for the longest series and
+// the largest zmax class, serve every trial. A zmax class owns only its
+// templates (taps and spectra), L-point twiddles and harmonic-sum tile
+// orders; per length only the real-FFT geometry and its twiddle tables
+// differ, cached as lightweight views of a class.
 // ---------------------------------------------------------------------------
 }  // extern "C"
 
 struct fdas_batch {
-  fdas_plan* base = nullptr;
-  std::vector<fdas_plan*> views;
+  fdas_plan* base = nullptr;          // class 0; owns every workspace
+  std::vector<fdas_plan*> classes;    // classes[0] == base; others share its workspaces
+  std::vector<fdas_plan*> views;      // (length, class) views other than the classes themselves
+  std::vector<int> view_cls;          // class of each view
   // captured CUDA graph of the last batch and the arguments it was made for
   bool graphs = true;
   cudaGraphExec_t exec = nullptr;
   std::vector<const float*> key_series;
   std::vector<int64_t> key_N;
+  std::vector<int32_t> key_zmax;
   fdas_cand* key_out = nullptr;
   int64_t* key_counts = nullptr;
   int64_t key_lane_gen = 0;  // the base's trial lane the graph was captured with (0: none)
@@ -818,35 +854,158 @@ struct fdas_batch {
 
 namespace {
 
-int batch_view(fdas_batch* b, int64_t N, fdas_plan** out) {
-  fdas_plan* base = b->base;
-  if (N == base->N) {
-    *out = base;
-    return FDAS_OK;
-  }
-  if (N > base->N) return set_error(FDAS_ERR_INVALID, "series longer than the batch's N_max");
-  for (fdas_plan* v : b->views)
-    if (v->N == N) {
-      *out = v;
-      return FDAS_OK;
-    }
-  fdas_plan* v = new fdas_plan(*base);  // shares the workspaces and templates
-  v->tw_M1 = v->tw_M2 = v->tw4_lo = v->tw4_hi = v->twN_lo = v->twN_hi = nullptr;
+// The per-trial workspaces of a class or view are the base plan's.
+void share_workspaces(fdas_plan* d, const fdas_plan* b) {
+  d->series = b->series; d->zbuf = b->zbuf; d->spec = b->spec; d->spec2 = b->spec2;
+  d->white = b->white; d->seg = b->seg; d->plane = b->plane; d->q4 = b->q4;
+  d->cands = b->cands; d->count = b->count; d->hs_list = b->hs_list; d->hs_nlist = b->hs_nlist;
+  d->plane_cap = b->plane_cap; d->seg_cap = b->seg_cap;
+}
+
+// A copy of plan b that owns nothing yet: every pointer it may free, and
+// every per-plan resource a search would make on first use, is cleared.
+fdas_plan* unowned_copy(const fdas_plan* b) {
+  fdas_plan* v = new fdas_plan(*b);
   v->hs_order[0] = v->hs_order[1] = nullptr;
   v->hs_order_w = 0;
-  v->lane = nullptr;  // batches run one trial after another on the base stream
+  v->lane = nullptr;  // batches fork the base's lane themselves
   v->ev_fork = v->ev_join = nullptr;
+  v->lane_gen = 0;
+  v->series2 = nullptr; v->series3[0] = v->series3[1] = nullptr;
+  v->cands2 = nullptr; v->count2 = nullptr; v->cstream = nullptr;
+  for (int k = 0; k < 4; ++k) v->ev_in[k] = v->ev_done[k] = nullptr;
+  v->dkeys = nullptr; v->dvals = nullptr; v->dbits = 0;
+  v->gbank = nullptr; v->gstatus = nullptr; v->taps_ib = nullptr; v->bank_ib = nullptr;
   v->device_bytes = 0;
+  return v;
+}
+
+void free_class(fdas_plan* c) {
+  void* ptrs[] = {c->tw_L, c->taps, c->bank};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  free_hs_order(c);
+  delete c;
+}
+
+void free_view(fdas_plan* v) {
+  free_geometry_tables(v);
+  free_hs_order(v);
+  delete v;
+}
+
+int class_index(const fdas_batch* b, int32_t zmax) {
+  for (size_t k = 0; k < b->classes.size(); ++k)
+    if (b->classes[k]->zmax == zmax) return (int)k;
+  return -1;
+}
+
+// Grows one of the base plan's workspaces (the stream is idle: the caller
+// synchronised it); the lane and any captured graph are dropped, since they
+// name the old buffers.
+template <typename T>
+int grow(fdas_batch* b, T** buf, int64_t* cap, int64_t need, int64_t elem_now) {
+  fdas_plan* base = b->base;
+  if (*cap >= need) return FDAS_OK;
+  cudaFree(*buf);
+  base->device_bytes -= (int64_t)sizeof(T) * elem_now;
+  *buf = nullptr;
+  *cap = 0;
+  int rc = dalloc(base, buf, (size_t)need);
+  if (rc) return rc;
+  *cap = need;
+  free_lane(base);
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return FDAS_OK;
+}
+
+// Adds the zmax class (zmax, m, L) to the batch: templates and tables of its
+// own, the base's workspaces grown to fit its plane and segment spectra.
+int add_class(fdas_batch* b, int32_t zmax, int32_t m, int32_t L) {
+  fdas_plan* base = b->base;
+  const int32_t dz = base->dz;
+  if (zmax < 0 || zmax % dz != 0)
+    return set_error(FDAS_ERR_INVALID, "class zmax must be >= 0 and a multiple of the batch's dz");
+  if (m < 8 || (m & 7)) return set_error(FDAS_ERR_INVALID, "template width must be a multiple of 8");
+  if (L != 2048 && L != 4096 && L != 8192)
+    return set_error(FDAS_ERR_INVALID, "segment length must be 2048, 4096 or 8192");
+  if (L < 2 * m) return set_error(FDAS_ERR_INVALID, "segment length must be >= 2 * width");
+  if (class_index(b, zmax) >= 0)
+    return set_error(FDAS_ERR_INVALID, "the batch already has a class for this zmax");
+  if ((int64_t)(2 * (zmax / dz) + 1) * base->nb > (int64_t(1) << 40))
+    return set_error(FDAS_ERR_INVALID, "plane too large");
+  int rc = cuda_check(cudaStreamSynchronize(base->stream), "sync");
+  if (rc) return rc;
+  fdas_plan* c = unowned_copy(base);
+  c->tw_L = nullptr; c->taps = nullptr; c->bank = nullptr;
+  c->zmax = zmax;
+  c->Z = 2 * (zmax / dz) + 1;
+  c->m = m;
+  c->L = L;
+  c->V = L - m;
+  c->S = (int)((c->nb + c->V - 1) / c->V);
+  if (!rc) rc = dalloc(c, &c->tw_L, (size_t)L);
+  if (!rc) rc = dalloc(c, &c->taps, (size_t)c->Z * m);
+  if (!rc) rc = dalloc(c, &c->bank, (size_t)c->Z * L);
+  if (!rc) rc = make_hs_order(c);
+  if (!rc) rc = launch_twiddles(c->tw_L, L, 1, L, c->stream);
+  if (!rc) rc = launch_template_taps(c);
+  if (!rc) rc = launch_template_bank(c);
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream), "class templates");
+  if (!rc)
+    rc = grow(b, &base->seg, &base->seg_cap, (int64_t)c->S * L, base->seg_cap);
+  if (!rc) {
+    const int64_t need = (int64_t)c->Z * base->nb;
+    if (base->plane_cap < need) {
+      cudaFree(base->q4);
+      base->device_bytes -= (int64_t)sizeof(float) * (base->plane_cap / 4);
+      base->q4 = nullptr;
+      rc = grow(b, &base->plane, &base->plane_cap, need, base->plane_cap);
+      if (!rc) rc = dalloc(base, &base->q4, (size_t)need / 4);
+    }
+  }
+  if (rc) {
+    free_class(c);
+    return rc;
+  }
+  base->device_bytes += c->device_bytes;
+  share_workspaces(c, base);
+  b->classes.push_back(c);
+  return FDAS_OK;
+}
+
+// The plan that runs a trial of length N in the class of zmax: the class
+// itself for N = N_max, else a cached view with that length's geometry.
+int batch_view(fdas_batch* b, int64_t N, int32_t zmax, fdas_plan** out) {
+  fdas_plan* base = b->base;
+  const int k = class_index(b, zmax);
+  if (k < 0) return set_error(FDAS_ERR_INVALID, "no class for this zmax (fdas_batch_add_class)");
+  if (N > base->N) return set_error(FDAS_ERR_INVALID, "series longer than the batch's N_max");
+  fdas_plan* c = b->classes[(size_t)k];
+  if (N == base->N) {
+    *out = c;
+    return FDAS_OK;
+  }
+  for (size_t i = 0; i < b->views.size(); ++i)
+    if (b->views[i]->N == N && b->view_cls[i] == k) {
+      *out = b->views[i];
+      return FDAS_OK;
+    }
+  fdas_plan* v = unowned_copy(c);  // shares the class's templates and tables
+  v->tw_M1 = v->tw_M2 = v->tw4_lo = v->tw4_hi = v->twN_lo = v->twN_hi = nullptr;
   int rc = set_geometry(v, N);
   if (!rc) rc = alloc_geometry_tables(v);
   if (!rc) rc = make_hs_order(v);
   if (rc) {
-    free_geometry_tables(v);
-    free_hs_order(v);
-    delete v;
+    free_view(v);
     return rc;
   }
+  base->device_bytes += v->device_bytes;
   b->views.push_back(v);
+  b->view_cls.push_back(k);
   *out = v;
   return FDAS_OK;
 }
@@ -929,8 +1088,14 @@ int fdas_batch_create(fdas_batch** out, int64_t N_max, int32_t zmax, int32_t dz,
   if (rc) return rc;
   fdas_batch* b = new fdas_batch();
   b->base = base;
+  b->classes.push_back(base);
   *out = b;
   return FDAS_OK;
+}
+
+int fdas_batch_add_class(fdas_batch* b, int32_t zmax, int32_t template_width, int32_t segment) {
+  if (!b) return set_error(FDAS_ERR_INVALID, "NULL batch");
+  return add_class(b, zmax, template_width, segment);
 }
 
 int fdas_batch_create_tuned(fdas_batch** out, int64_t N_max, int32_t zmax, int32_t dz,
@@ -938,6 +1103,7 @@ int fdas_batch_create_tuned(fdas_batch** out, int64_t N_max, int32_t zmax, int32
                             const float* d_probe, void* stream) {
   if (!out) return set_error(FDAS_ERR_INVALID, "out is NULL");
   *out = nullptr;
+  if (int e = check_aligned(d_probe, 8, "d_probe")) return e;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int32_t cand[3] = {2048, 4096, 8192};
   float* own = nullptr;
@@ -994,7 +1160,11 @@ int fdas_batch_get_info(const fdas_batch* b, fdas_batch_info* info) {
   memset(info, 0, sizeof(*info));
   info->N_max = b->base->N;
   info->segment = b->base->L;
-  info->n_lengths = 1 + (int32_t)b->views.size();
+  // distinct series lengths with a geometry
+  std::vector<int64_t> lens{b->base->N};
+  for (const fdas_plan* v : b->views)
+    if (std::find(lens.begin(), lens.end(), v->N) == lens.end()) lens.push_back(v->N);
+  info->n_lengths = (int32_t)lens.size();
   info->graphs = b->graphs && b->base->stream != nullptr;
   info->graph_builds = b->graph_builds;
   info->graph_launches = b->graph_launches;
@@ -1005,6 +1175,8 @@ int fdas_batch_get_info(const fdas_batch* b, fdas_batch_info* info) {
     info->tuned_hs_block[i] = b->tuned_hs[i];
     info->tuned_ms[i] = b->tuned_ms[i];
   }
+  info->n_classes = (int32_t)b->classes.size();
+  info->device_bytes = b->base->device_bytes;
   return FDAS_OK;
 }
 
@@ -1012,27 +1184,34 @@ int fdas_batch_destroy(fdas_batch* b) {
   if (!b) return FDAS_OK;
   if (b->base && b->base->stream) cudaStreamSynchronize(b->base->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
-  for (fdas_plan* v : b->views) {
-    free_geometry_tables(v);
-    free_hs_order(v);
-    delete v;
-  }
+  for (fdas_plan* v : b->views) free_view(v);
+  for (size_t k = 1; k < b->classes.size(); ++k) free_class(b->classes[k]);
   fdas_plan_destroy(b->base);
   delete b;
   return FDAS_OK;
 }
 
 int fdas_search_batch(fdas_batch* b, const float* const* d_series, const int64_t* N,
-                      int32_t n_trials, fdas_cand* d_out, int64_t* d_counts) {
+                      const int32_t* zmax, int32_t n_trials, fdas_cand* d_out,
+                      int64_t* d_counts) {
   if (!b || !d_series || !N || n_trials < 0 || (n_trials > 0 && (!d_out || !d_counts)))
     return set_error(FDAS_ERR_INVALID, "bad argument to fdas_search_batch");
-  // every length's geometry first: allocations cannot be captured
+  if (n_trials > 0) {
+    if (int rc = check_aligned(d_out, 4, "d_out")) return rc;
+    if (int rc = check_aligned(d_counts, 8, "d_counts")) return rc;
+  }
+  // every (length, class) geometry first: allocations cannot be captured
   std::vector<fdas_plan*> vs((size_t)n_trials);
+  std::vector<int32_t> zs((size_t)n_trials);
   for (int32_t t = 0; t < n_trials; ++t) {
     if (!d_series[t]) return set_error(FDAS_ERR_INVALID, "NULL series in batch");
-    int rc = batch_view(b, N[t], &vs[t]);
+    if (int rc = check_aligned(d_series[t], 8, "d_series[t]")) return rc;
+    zs[(size_t)t] = zmax ? zmax[t] : b->base->zmax;
+    int rc = batch_view(b, N[t], zs[(size_t)t], &vs[(size_t)t]);
     if (rc) return rc;
   }
+  for (size_t k = 1; k < b->classes.size(); ++k) share_workspaces(b->classes[k], b->base);
+  for (fdas_plan* v : b->views) share_workspaces(v, b->base);
   if (n_trials > 1 && lanes_usable(b->base)) {
     int rc = ensure_lane(b->base);
     if (rc) return rc;
@@ -1045,7 +1224,8 @@ int fdas_search_batch(fdas_batch* b, const float* const* d_series, const int64_t
                     b->key_lane_gen == (b->base->lane ? b->base->lane_gen : 0) &&
                     b->key_series.size() == (size_t)n_trials &&
                     std::equal(b->key_series.begin(), b->key_series.end(), d_series) &&
-                    std::equal(b->key_N.begin(), b->key_N.end(), N);
+                    std::equal(b->key_N.begin(), b->key_N.end(), N) &&
+                    std::equal(b->key_zmax.begin(), b->key_zmax.end(), zs.begin());
   if (!same) {
     int rc = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal),
                         "begin capture");
@@ -1077,6 +1257,7 @@ int fdas_search_batch(fdas_batch* b, const float* const* d_series, const int64_t
     ++b->graph_builds;
     b->key_series.assign(d_series, d_series + n_trials);
     b->key_N.assign(N, N + n_trials);
+    b->key_zmax = zs;
     b->key_out = d_out;
     b->key_counts = d_counts;
     b->key_lane_gen = b->base->lane ? b->base->lane_gen : 0;

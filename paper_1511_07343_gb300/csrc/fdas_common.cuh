@@ -91,10 +91,10 @@ FDAS_DEV void dft(float2 (&x)[R]) {
   for (int k = 0; k < R; ++k) x[k] = y[k];
 }
 
-// Radix used by stage s of a length-L Stockham FFT: 16 while at least 16
-// remains, then the leftover factor (2, 4 or 8).
+// Radix used by the stage of a length-L Stockham FFT that starts at span ns:
+// 16 while more than 32 points remain, then a single radix-32 stage if
+// exactly 32 remain, else the leftover factor (2, 4, 8 or 16).
 __host__ __device__ constexpr int stage_radix(int L, int ns) {
-  // radix 16 while more than 32 points remain; a final 32 is one stage
   return (L / ns) == 32 ? 32 : (L / ns) >= 16 ? 16 : (L / ns);
 }
 

@@ -38,9 +38,11 @@
 //              (tcgen05.ld), form |A|^2 and store the plane rows
 //   warp 4     producer: bulk copies of template-bank blocks
 //   warp 5     issues tcgen05.mma (one thread) and the commits
-// Every wait is bounded; a wait that gives up sets the plan's status word
-// and all roles leave their loops; the kernel still retires its MMAs and
-// copies and frees TMEM before it returns.
+// Every wait is bounded; a pipeline wait that gives up (after the plan's
+// poll limit, 2^23 polls by default) sets the plan's status word and all
+// roles leave their loops; the kernel still waits, with the full fixed bound
+// and whatever the plan's limit, for the bulk copies it issued and the MMAs
+// it committed, and frees TMEM, before it returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -60,6 +62,7 @@ constexpr int kGmWBufs = 1;                    // Hankel buffers (the room goes 
 constexpr int kGmStageBytes = kGmMT * kGmKB * 2;  // 16 KB
 constexpr int kGmThreads = 192;
 constexpr uint32_t kGmSpin = 1u << 23;         // polls of one bounded wait (~1 s)
+// (kGmSpin is the default pipeline limit and the fixed bound of the drains)
 
 // K sections 0..5 read shared-memory parts 2, 3, 0, 1, 0, 1 (0 Re hi, 1 Im hi,
 // 2 Re lo, 3 Im lo)
@@ -108,10 +111,12 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase of parity `parity`; false when it gave up or
-// another role already did (the abort word is then set).
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* status) {
-  for (uint32_t i = 0; i < kGmSpin; ++i) {
+// Bounded pipeline wait for the phase of parity `parity` (at most `limit`
+// polls); false when it gave up or another role already did (the abort word
+// is then set).
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* status,
+                          uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i) {
     if (mbar_test(bar, parity)) return true;
     if ((i & 63u) == 63u) {
       if (*abort) return false;
@@ -121,6 +126,17 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, in
   *abort = 1;
   atomicExch(status, FDAS_ERR_TIMEOUT);
   return false;
+}
+
+// Wait for a completion that arrives on its own (a bulk copy landing, a
+// commit of MMAs already issued) before the CTA frees what it uses: the full
+// fixed bound, not the plan's limit, and no early exit on abort.
+__device__ void mbar_drain(uint32_t bar, uint32_t parity, int* status) {
+  for (uint32_t i = 0; i < kGmSpin; ++i) {
+    if (mbar_test(bar, parity)) return;
+    if ((i & 63u) == 63u) __nanosleep(64);
+  }
+  atomicExch(status, FDAS_ERR_TIMEOUT);
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
@@ -265,7 +281,7 @@ template <typename T>
 __global__ void __launch_bounds__(kGmThreads, 1)
     k_gemm_correlate(const uint16_t* __restrict__ bank, const float2* __restrict__ white,
                      float* __restrict__ plane, int* __restrict__ status, int64_t nb, int Z,
-                     int m, int nMT, int nKB, int nRT) {
+                     int m, int nMT, int nKB, int nRT, uint32_t spin) {
   using E = Elt<T>;
   extern __shared__ __align__(1024) uint8_t smem[];
   const GemmLayout g = gemm_layout(m);
@@ -355,7 +371,7 @@ __global__ void __launch_bounds__(kGmThreads, 1)
       const int64_t r0 = (int64_t)(blockIdx.x + (int64_t)q * gridDim.x) * kGmNT;
       for (int mt = 0; mt < nMT; ++mt, ++tile) {
         int got = 0;
-        if (lane == 0) got = mbar_wait(bar_tfull, tile & 1u, abort, status) ? 1 : 0;
+        if (lane == 0) got = mbar_wait(bar_tfull, tile & 1u, abort, status, spin) ? 1 : 0;
         got = __shfl_sync(0xffffffffu, got, 0);
         if (!got) {
           ok = false;
@@ -401,7 +417,7 @@ __global__ void __launch_bounds__(kGmThreads, 1)
         for (int b = 0; b < per_block; ++b, ++it) {
           const int s = it % kGmStages;
           if (it >= (uint32_t)kGmStages &&
-              !mbar_wait(bar_empty(s), ((it / kGmStages) - 1) & 1u, abort, status)) {
+              !mbar_wait(bar_empty(s), ((it / kGmStages) - 1) & 1u, abort, status, spin)) {
             ok = false;
             break;
           }
@@ -412,7 +428,7 @@ __global__ void __launch_bounds__(kGmThreads, 1)
       // copies still in flight land before the CTA may exit
       const uint32_t first = it > (uint32_t)kGmStages ? it - kGmStages : 0;
       for (uint32_t k = first; k < it; ++k)
-        mbar_wait(bar_full(k % kGmStages), (k / kGmStages) & 1u, abort, status);
+        mbar_drain(bar_full(k % kGmStages), (k / kGmStages) & 1u, status);
     }
   } else {
     // ---------------------------------------------- MMA issuer
@@ -427,10 +443,10 @@ __global__ void __launch_bounds__(kGmThreads, 1)
         const uint32_t wb = w_base + (uint32_t)(q % kGmWBufs) * g.w_buf;
         const uint64_t w_desc0 = sdesc(wb, 128u, 128u);  // part pt at + pt * w_part / 16
         if (!mbar_wait(bar_wfull0 + 8u * (q % kGmWBufs), (uint32_t)(q / kGmWBufs) & 1u, abort,
-                       status))
+                       status, spin))
           break;
         for (int mt = 0; mt < nMT && ok; ++mt, ++tile) {
-          if (tile > 0 && !mbar_wait(bar_tempty, (tile - 1) & 1u, abort, status)) {
+          if (tile > 0 && !mbar_wait(bar_tempty, (tile - 1) & 1u, abort, status, spin)) {
             ok = false;
             break;
           }
@@ -438,7 +454,7 @@ __global__ void __launch_bounds__(kGmThreads, 1)
           int sec = 0, d0 = 0;  // K section and tap offset of the next K step
           for (int kb = 0; kb < nKB; ++kb, ++it) {
             const int s = it % kGmStages;
-            if (!mbar_wait(bar_full(s), (it / kGmStages) & 1u, abort, status)) {
+            if (!mbar_wait(bar_full(s), (it / kGmStages) & 1u, abort, status, spin)) {
               ok = false;
               break;
             }
@@ -466,7 +482,7 @@ __global__ void __launch_bounds__(kGmThreads, 1)
       }
       // every MMA issued above has retired once this commit lands
       umma_commit(bar_done);
-      mbar_wait(bar_done, 0, abort, status);
+      mbar_drain(bar_done, 0, status);
     }
   }
   tmem_fence_before_sync();
@@ -508,7 +524,8 @@ int gemm_run(fdas_plan* p, float* d_plane) {
   if (e != cudaSuccess) return cuda_check(e, "SM count");
   const int grid = std::min(sms, nRT);
   k_gemm_correlate<T><<<grid, kGmThreads, g.total, p->stream>>>(
-      p->gbank, p->white, d_plane, p->gstatus, p->nb, p->Z, p->m, nMT, nKB, nRT);
+      p->gbank, p->white, d_plane, p->gstatus, p->nb, p->Z, p->m, nMT, nKB, nRT,
+      p->gm_spin ? p->gm_spin : kGmSpin);
   return cuda_check(cudaGetLastError(), "k_gemm_correlate");
 }
 

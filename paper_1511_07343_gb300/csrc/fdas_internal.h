@@ -64,12 +64,14 @@ struct fdas_plan {
   double2* taps_ib = nullptr;
   float2* bank_ib = nullptr;
   int64_t plane_cap = 0;       // floats the plane buffer holds (Q4: plane_cap / 4)
+  int64_t seg_cap = 0;         // float2 the segment buffer holds (>= S L)
   // candidate distillation: hash table of 2^dbits keys and values (on first use)
   unsigned long long* dkeys = nullptr;
   float* dvals = nullptr;
   int dbits = 0;
   uint16_t* gbank = nullptr;   // 16-bit left factor, pre-tiled (see fdas_gemm.cu)
   int* gstatus = nullptr;      // device status word of the bounded waits
+  uint32_t gm_spin = 0;        // poll limit of its pipeline waits (0: the default, ~1 s)
 
   // host-input pipeline (more staging buffers, a second candidate list and
   // count, a copy stream and events; made on the first multi-trial host
@@ -110,6 +112,17 @@ inline int64_t plane_width(const fdas_plan* p) { return p->nb << p->interbin; }
 // error plumbing
 int set_error(int code, const std::string& msg);
 int cuda_check(cudaError_t e, const char* what);
+
+// A caller's device pointer must be aligned for the vector accesses the
+// kernels make through it (8 bytes where they read or write float2, 16 where
+// float4, 8 for the 64-bit counters); checked before any device work, so a
+// misaligned view (say a tensor sliced at an odd float) is an argument error
+// rather than a misaligned-address fault.
+inline int check_aligned(const void* ptr, uintptr_t bytes, const char* what) {
+  if ((reinterpret_cast<uintptr_t>(ptr) & (bytes - 1)) == 0) return 0;
+  return set_error(FDAS_ERR_INVALID, std::string(what) + " must be " + std::to_string(bytes) +
+                                         "-byte aligned");
+}
 
 // fdas_templates.cu
 int launch_twiddles(float2* out, int64_t count, int64_t mult, int64_t period, cudaStream_t s);

@@ -10,6 +10,8 @@
 // array below, which exists on every GPU that loads this library until the
 // process exits. Nothing here calls cudaMalloc, cudaFree or any allocating
 // routine.
+#include <atomic>
+
 #include "fdas_internal.h"
 
 namespace fdas {
@@ -24,22 +26,29 @@ constexpr int64_t kScratchSlots = 2 * kMaxM + 6 * (kMaxTab + 1);
 static __device__ __align__(256) float2 g_noalloc_scratch[kScratchSlots];
 
 // Device address of the array, looked up once per device (the first call on
-// a device does this, with that device current).
+// a device does this, with that device current). Host threads that make
+// their first calls at the same time may each look it up; they store the
+// same address, and the atomic slots make that well defined. The address
+// belongs to the device's context at the time of the lookup: after
+// cudaDeviceReset the module is loaded again, possibly elsewhere, so a
+// process that resets a device must not call this entry point on it again.
 constexpr int kMaxDevices = 64;
-float2* g_scratch_ptr[kMaxDevices] = {nullptr};
+std::atomic<float2*> g_scratch_ptr[kMaxDevices];
 
 int scratch_for_current_device(float2** out) {
   int dev = 0;
   int rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
   if (rc) return rc;
   if (dev < 0 || dev >= kMaxDevices) return set_error(FDAS_ERR_INVALID, "device ordinal too large");
-  if (!g_scratch_ptr[dev]) {
+  float2* cached = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!cached) {
     void* p = nullptr;
     rc = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
     if (rc) return rc;
-    g_scratch_ptr[dev] = static_cast<float2*>(p);
+    cached = static_cast<float2*>(p);
+    g_scratch_ptr[dev].store(cached, std::memory_order_release);
   }
-  *out = g_scratch_ptr[dev];
+  *out = cached;
   return FDAS_OK;
 }
 
@@ -57,6 +66,9 @@ using namespace fdas;
 extern "C" int fdas_spectrum_noalloc(const float* d_series, int64_t N, float* d_spectrum,
                                      void* stream) {
   if (!d_series || !d_spectrum) return set_error(FDAS_ERR_INVALID, "NULL argument");
+  // the kernels read the series and write the spectrum as float2
+  if (int e = check_aligned(d_series, 8, "d_series")) return e;
+  if (int e = check_aligned(d_spectrum, 8, "d_spectrum")) return e;
   if (N < (1 << 12) || N > kNoallocMaxN || (N & (N - 1)) != 0)
     return set_error(FDAS_ERR_INVALID,
                      "fdas_spectrum_noalloc: N must be a power of two in [2^12, 2^20]; larger "

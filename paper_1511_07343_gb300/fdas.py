@@ -49,7 +49,8 @@ class fdas_batch_info(ctypes.Structure):
                 ("n_tuned", ctypes.c_int32), ("graph_builds", ctypes.c_int64),
                 ("graph_launches", ctypes.c_int64), ("hs_block", ctypes.c_int32),
                 ("tuned_segment", ctypes.c_int32 * 8), ("tuned_hs_block", ctypes.c_int32 * 8),
-                ("tuned_ms", ctypes.c_float * 8)]
+                ("tuned_ms", ctypes.c_float * 8), ("n_classes", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64)]
 
 
 CAND_DTYPE = np.dtype([("r_top", "<i4"), ("z_idx", "<i4"), ("h", "<i4"), ("power", "<f4")])
@@ -79,7 +80,8 @@ _SIGS = {
     "fdas_batch_create": [ctypes.POINTER(_P), _I64, _I32, _I32, _I32, _I32, _I32,
                           ctypes.c_float, _I64, _P],
     "fdas_batch_destroy": [_P],
-    "fdas_search_batch": [_P, _P, _P, _I32, _P, _P],
+    "fdas_batch_add_class": [_P, _I32, _I32, _I32],
+    "fdas_search_batch": [_P, _P, _P, _P, _I32, _P, _P],
     "fdas_plane_debug": [_P, _P],
     "fdas_stage_spectrum": [_P, _P, _P],
     "fdas_stage_whiten": [_P, _P, _P],
@@ -93,6 +95,7 @@ _SIGS = {
     "fdas_plan_set_whitening": [_P, _I32],
     "fdas_plan_set_harmsum_block": [_P, _I32],
     "fdas_plan_set_interbin": [_P, _I32],
+    "fdas_plan_set_wait_limit": [_P, ctypes.c_uint32],
     "fdas_distill": [_P, _P, _P, _P, _P],
     "fdas_batch_create_tuned": [ctypes.POINTER(_P), _I64, _I32, _I32, _I32, _I32,
                                 ctypes.c_float, _I64, _P, _P],
@@ -216,13 +219,24 @@ def fdas_batch_destroy(batch):
     _check(load().fdas_batch_destroy(batch), "fdas_batch_destroy")
 
 
-def fdas_search_batch(batch, d_series_list, N_list, d_out, d_counts):
+def fdas_batch_add_class(batch, zmax, template_width, segment):
+    _check(load().fdas_batch_add_class(batch, zmax, template_width, segment),
+           "fdas_batch_add_class")
+
+
+def fdas_search_batch(batch, d_series_list, N_list, d_out, d_counts, zmax_list=None):
     n = len(d_series_list)
     ptrs = (ctypes.c_void_p * n)(*[_ptr(x) for x in d_series_list])
     lens = (ctypes.c_int64 * n)(*[int(v) for v in N_list])
+    zs = None
+    if zmax_list is not None:
+        if len(zmax_list) != n:
+            raise ValueError("zmax_list needs one entry per trial")
+        zs = (ctypes.c_int32 * n)(*[int(v) for v in zmax_list])
     _check(load().fdas_search_batch(batch, ctypes.cast(ptrs, ctypes.c_void_p),
-                                    ctypes.cast(lens, ctypes.c_void_p), n, _ptr(d_out),
-                                    _ptr(d_counts)), "fdas_search_batch")
+                                    ctypes.cast(lens, ctypes.c_void_p),
+                                    ctypes.cast(zs, ctypes.c_void_p) if zs is not None else None,
+                                    n, _ptr(d_out), _ptr(d_counts)), "fdas_search_batch")
 
 
 def fdas_plane_debug(plan, d_plane):
@@ -276,6 +290,10 @@ def fdas_plan_set_whitening(plan, mode):
 
 def fdas_plan_set_harmsum_block(plan, threads):
     _check(load().fdas_plan_set_harmsum_block(plan, threads), "fdas_plan_set_harmsum_block")
+
+
+def fdas_plan_set_wait_limit(plan, polls):
+    _check(load().fdas_plan_set_wait_limit(plan, int(polls)), "fdas_plan_set_wait_limit")
 
 
 def fdas_plan_set_correlation(plan, mode):

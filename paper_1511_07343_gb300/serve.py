@@ -2,18 +2,24 @@
 
 De-dispersion produces many trials (~6000 per 530 s SKA observation,
 Section 1) of possibly different lengths and acceleration ranges. A
-`Server` keeps device-resident plans (templates, twiddle tables, workspaces)
-in worker slots, each slot with its own CUDA stream and host thread:
+`Server` keeps device-resident search state in worker slots, each slot with
+its own CUDA stream and host thread:
 
-* requests (host series + zmax) enter a FIFO queue as they arrive;
-* an idle slot takes the next request at once; a slot builds the plan of a
-  zmax class the first time it needs it, and only if the device-memory
-  budget still has room for that plan's footprint (otherwise the request
-  waits for a slot that already holds such a plan);
-* each slot copies its series to the device, enqueues the whole search on
-  its stream (the same C ABI entry point as a single search) and returns the
-  candidates; slots run concurrently, so work from different requests
-  overlaps on the GPU.
+* every slot holds one batch object of the C library with a zmax class per
+  acceleration range served (templates and tables per class; one set of
+  per-trial workspaces sized for the largest class, plus a second trial
+  lane), built when the server starts;
+* admission is by HBM footprint: the server starts only as many slots as the
+  device-memory budget holds (a slot's footprint is fixed, so a request that
+  a slot takes always fits);
+* requests (host series + zmax) enter a FIFO queue as they arrive; an idle
+  slot takes the oldest request and, without waiting, up to ``max_batch - 1``
+  more that are already queued, and runs them as ONE fdas_search_batch call
+  (mixed lengths and zmax classes; consecutive trials overlap on the slot's
+  two lanes); slots run concurrently, so work from different requests
+  overlaps on the GPU while new ones keep arriving;
+* a request cancelled while queued is skipped; results are sorted candidate
+  lists, the same as a single search of that trial gives.
 
 Every arithmetic step runs in the CUDA library; this module only schedules.
 """
@@ -33,42 +39,44 @@ from . import fdas
 # pattern of the SKA-shaped configurations).
 DEFAULT_CLASSES = {50: (128, 2048), 100: (256, 4096), 200: (512, 8192)}
 
+_HS_LIST_BYTES = 8 << 20   # the harmonic-sum screen's list of 2^20 flagged pairs
+
+
+def _trial_workspace_bytes(n_max: int, Z: int, seg_floats2: int, max_cands: int) -> int:
+    """Per-trial workspaces of one lane: staging series, four-step scratch,
+    spectra, segment spectra, plane and 4-bin maxima, candidate list,
+    flagged-pair list."""
+    nb = n_max // 2
+    return (4 * n_max + 8 * 4 * nb + 8 * seg_floats2 + 5 * Z * nb + 16 * max_cands
+            + _HS_LIST_BYTES)
+
 
 def plan_footprint(n_max: int, zmax: int, m: int, L: int, dz: int = 2,
                    max_cands: int = 1 << 20) -> int:
-    """Device bytes a plan of this class holds, for admission: plane and its
-    4-bin maxima, spectra and workspaces, segment spectra, templates, the
-    candidate list and the harmonic-sum screen's list of 2^20 flagged pairs
-    (an upper estimate of fdas_plan_get_info's device_bytes)."""
+    """Device bytes one plan of this class holds (an upper estimate of
+    fdas_plan_get_info's device_bytes): its per-trial workspaces plus the
+    templates (float64 taps and float32 spectra) and tables."""
     Z = 2 * (zmax // dz) + 1
     nb = n_max // 2
     S = (nb + (L - m) - 1) // (L - m)
-    core = (4 * Z * nb + Z * nb + 8 * 4 * nb + 8 * S * L + 24 * Z * L
-            + 16 * max_cands + 4 * n_max + 8 * (1 << 20))
-    # twiddle tables and counters (a few MB at most), plus 2% headroom
+    core = _trial_workspace_bytes(n_max, Z, S * L, max_cands) + 24 * Z * L
+    # twiddle tables, tile orders and counters (a few MB at most), plus 2% headroom
     return int(core * 1.02) + (8 << 20)
 
 
-class Budget:
-    """Thread-safe reservation of a fixed number of device bytes."""
-
-    def __init__(self, total: int):
-        self.total = int(total)
-        self.reserved = 0
-        self._lock = threading.Lock()
-
-    def try_reserve(self, nbytes: int) -> bool:
-        with self._lock:
-            if self.reserved + nbytes > self.total:
-                return False
-            self.reserved += nbytes
-            return True
-
-    def release(self, nbytes: int):
-        with self._lock:
-            if nbytes > self.reserved:
-                raise ValueError("release of bytes never reserved")
-            self.reserved -= nbytes
+def batch_footprint(n_max: int, classes: dict, dz: int = 2, max_cands: int = 1 << 20,
+                    lanes: bool = True) -> int:
+    """Device bytes of one multi-class batch (an upper estimate of
+    fdas_batch_get_info's device_bytes): one set of per-trial workspaces sized
+    for the largest class (two with the second trial lane) plus every class's
+    templates and tables."""
+    nb = n_max // 2
+    Zmax = max(2 * (z // dz) + 1 for z in classes)
+    seg = max(((nb + (L - m) - 1) // (L - m)) * L for (m, L) in classes.values())
+    ws = _trial_workspace_bytes(n_max, Zmax, seg, max_cands)
+    tables = sum(24 * (2 * (z // dz) + 1) * L + (2 << 20) for z, (m, L) in classes.items())
+    core = ws * (2 if lanes else 1) + tables
+    return int(core * 1.02) + (8 << 20)
 
 
 @dataclasses.dataclass
@@ -79,6 +87,7 @@ class Result:
     n: int
     arrival: float              # time.perf_counter() at submit
     done: float                 # time.perf_counter() when the result was ready
+    batch: int = 1              # trials in the fdas_search_batch call that served it
 
     @property
     def latency_ms(self) -> float:
@@ -96,30 +105,42 @@ class _Request:
 class Server:
     def __init__(self, n_max: int, n_slots: int = 2, hbm_budget: int | None = None,
                  classes=None, dz: int = 2, nharm: int = 16, sigma: float = 6.0,
-                 max_cands: int = 1 << 20, device: int = 0):
+                 max_cands: int = 1 << 20, device: int = 0, max_batch: int = 2):
         import torch
         self._torch = torch
         self.n_max = int(n_max)
         self.classes = dict(classes or DEFAULT_CLASSES)
         self.dz, self.nharm, self.sigma, self.max_cands = dz, nharm, sigma, max_cands
+        self.max_batch = max(1, int(max_batch))
         self.device = torch.device("cuda", device)
         if hbm_budget is None:
             free, _ = torch.cuda.mem_get_info(self.device)
             hbm_budget = int(0.8 * free)
         self.hbm_budget = int(hbm_budget)
-        self._budget = Budget(self.hbm_budget)
+        self.slot_bytes = batch_footprint(self.n_max, self.classes, dz, max_cands,
+                                          lanes=self.max_batch > 1)
+        n_fit = min(int(n_slots), self.hbm_budget // self.slot_bytes)
         self._lock = threading.Lock()
         self._queue: "queue.Queue[_Request | None]" = queue.Queue()
-        self._slots = [_Slot(self, i) for i in range(n_slots)]
+        self.stats = {"slots": n_fit, "admitted": 0, "batches": 0, "cancelled": 0,
+                      "largest_batch": 0}
+        self._slots = []
         self._closed = False
-        self.stats = {"admitted": 0, "plans_built": 0, "waits_for_memory": 0}
+        try:
+            for i in range(n_fit):
+                self._slots.append(_Slot(self, i))
+        except Exception:
+            for s in self._slots:
+                s.release()
+            raise
         for s in self._slots:
             s.start()
 
     # -- public API ---------------------------------------------------------
     def submit(self, series: np.ndarray, zmax: int) -> cf.Future:
         """Queue one DM trial (host float32 series); the future resolves to a
-        Result."""
+        Result. Cancelling the future before a slot takes the request drops
+        the request."""
         if self._closed:
             raise RuntimeError("server is closed")
         if zmax not in self.classes:
@@ -127,8 +148,9 @@ class Server:
         x = np.ascontiguousarray(series, dtype=np.float32)
         if x.shape[0] > self.n_max:
             raise ValueError("series longer than the server's n_max")
-        if self._footprint(int(zmax)) > self.hbm_budget:
-            raise ValueError("one plan of this class does not fit in the memory budget")
+        if not self._slots:
+            raise ValueError("not one slot fits in the memory budget "
+                             f"({self.slot_bytes} bytes per slot, budget {self.hbm_budget})")
         fut: cf.Future = cf.Future()
         self._queue.put(_Request(x, int(zmax), fut, time.perf_counter()))
         return fut
@@ -150,16 +172,45 @@ class Server:
     def __exit__(self, *a):
         self.close()
 
-    # -- admission ------------------------------------------------------------
-    def _footprint(self, zmax: int) -> int:
-        m, L = self.classes[zmax]
-        return plan_footprint(self.n_max, zmax, m, L, self.dz, self.max_cands)
+    # -- scheduling -----------------------------------------------------------
+    def _take(self):
+        """The oldest request (blocking) plus up to max_batch - 1 more already
+        queued; None when the server is closing. Requests cancelled while
+        queued are dropped here: set_running_or_notify_cancel() marks the
+        others running, after which they can no longer be cancelled."""
+        got, stop = [], False
+        req = self._queue.get()
+        if req is None:
+            return None
+        pending = [req]
+        while len(pending) < self.max_batch:
+            try:
+                nxt = self._queue.get_nowait()
+            except queue.Empty:
+                break
+            if nxt is None:       # closing: finish this batch, then stop
+                stop = True
+                break
+            pending.append(nxt)
+        for r in pending:
+            if r.future.set_running_or_notify_cancel():
+                got.append(r)
+            else:
+                with self._lock:
+                    self.stats["cancelled"] += 1
+        return got, stop
 
-    def _try_reserve(self, nbytes: int) -> bool:
-        return self._budget.try_reserve(nbytes)
 
-    def _release(self, nbytes: int):
-        self._budget.release(nbytes)
+def _settle(fut: cf.Future, result=None, error: BaseException | None = None):
+    """Completes a running future; a future that is already done is left as
+    it is (never raises into the slot thread)."""
+    try:
+        if error is not None:
+            fut.set_exception(error)
+        else:
+            fut.set_result(result)
+    except cf.InvalidStateError:
+        pass
 
 
 class _Slot(threading.Thread):
@@ -168,74 +219,78 @@ class _Slot(threading.Thread):
         self.s = server
         torch = server._torch
         self.stream = torch.cuda.Stream(server.device)
-        self.batches: dict[int, int] = {}     # zmax -> fdas_batch handle
-        self.bytes: dict[int, int] = {}
-        self.d_series = torch.empty(server.n_max, dtype=torch.float32, device=server.device)
-        self.h_series = torch.empty(server.n_max, dtype=torch.float32).pin_memory()
-        self.d_out = torch.empty(server.max_cands * 16, dtype=torch.uint8, device=server.device)
-        self.d_cnt = torch.zeros(1, dtype=torch.int64, device=server.device)
-
-    def _batch_for(self, zmax: int):
-        if zmax in self.batches:
-            return self.batches[zmax]
-        s = self.s
-        need = s._footprint(zmax)
-        if not s._try_reserve(need):
-            # this slot is idle, so its plans of other classes can go
-            self.release()
-            if not s._try_reserve(need):
-                return None
-        m, L = s.classes[zmax]
+        B = server.max_batch
+        self.d_series = [torch.empty(server.n_max, dtype=torch.float32, device=server.device)
+                         for _ in range(B)]
+        self.h_series = [torch.empty(server.n_max, dtype=torch.float32).pin_memory()
+                         for _ in range(B)]
+        self.d_out = torch.empty(B * server.max_cands * 16, dtype=torch.uint8,
+                                 device=server.device)
+        self.d_cnt = torch.zeros(B, dtype=torch.int64, device=server.device)
+        zs = sorted(server.classes, reverse=True)   # the largest class first
+        m, L = server.classes[zs[0]]
+        self.batch = fdas.fdas_batch_create(server.n_max, zs[0], server.dz, m, L, server.nharm,
+                                            server.sigma, server.max_cands,
+                                            self.stream.cuda_stream)
         try:
-            b = fdas.fdas_batch_create(s.n_max, zmax, s.dz, m, L, s.nharm, s.sigma, s.max_cands,
-                                       self.stream.cuda_stream)
+            for z in zs[1:]:
+                fdas.fdas_batch_add_class(self.batch, z, *server.classes[z])
+            # the mix changes from call to call, so launch directly rather
+            # than capture a graph per call
+            fdas.fdas_batch_set_graphs(self.batch, 0)
         except Exception:
-            s._release(need)
+            fdas.fdas_batch_destroy(self.batch)
+            self.batch = None
             raise
-        self.batches[zmax] = b
-        self.bytes[zmax] = need
-        with s._lock:
-            s.stats["plans_built"] += 1
-        return b
 
     def run(self):
         torch = self.s._torch
         torch.cuda.set_device(self.s.device)
         while True:
-            req = self.s._queue.get()
-            if req is None:
+            taken = self.s._take()
+            if taken is None:
                 return
-            try:
-                b = self._batch_for(req.zmax)
-                if b is None:
-                    # no memory for a new plan: hand the request back and let a
-                    # slot that holds this class (or a later free-up) take it
+            reqs, stop = taken
+            if reqs:
+                try:
+                    results = self._serve(reqs)
                     with self.s._lock:
-                        self.s.stats["waits_for_memory"] += 1
-                    self.s._queue.put(req)
-                    time.sleep(0.001)
-                    continue
-                with self.s._lock:
-                    self.s.stats["admitted"] += 1
-                req.future.set_result(self._serve(b, req))
-            except Exception as e:  # the error goes to the caller's future
-                req.future.set_exception(e)
+                        self.s.stats["admitted"] += len(reqs)
+                        self.s.stats["batches"] += 1
+                        self.s.stats["largest_batch"] = max(self.s.stats["largest_batch"],
+                                                            len(reqs))
+                    for r, res in zip(reqs, results):
+                        _settle(r.future, res)
+                except Exception as e:  # the error goes to every caller's future
+                    for r in reqs:
+                        _settle(r.future, error=e)
+            if stop:
+                return
 
-    def _serve(self, batch, req: _Request) -> Result:
+    def _serve(self, reqs) -> list:
         torch = self.s._torch
-        n = req.series.shape[0]
+        ns = [r.series.shape[0] for r in reqs]
+        M = self.s.max_cands
         with torch.cuda.stream(self.stream):
-            self.h_series[:n].numpy()[:] = req.series
-            self.d_series[:n].copy_(self.h_series[:n], non_blocking=True)
-            fdas.fdas_search_batch(batch, [self.d_series], [n], self.d_out, self.d_cnt)
-            cnt = int(self.d_cnt.to("cpu", non_blocking=False).item())
-            keep = min(cnt, self.s.max_cands)
-            raw = self.d_out[: keep * 16].to("cpu").numpy().view(fdas.CAND_DTYPE).copy()
-        raw.sort(order=["h", "r_top", "z_idx"])
-        return Result(raw, cnt, req.zmax, n, req.arrival, time.perf_counter())
+            for i, r in enumerate(reqs):
+                self.h_series[i][: ns[i]].numpy()[:] = r.series
+                self.d_series[i][: ns[i]].copy_(self.h_series[i][: ns[i]], non_blocking=True)
+            fdas.fdas_search_batch(self.batch, self.d_series[: len(reqs)], ns, self.d_out,
+                                   self.d_cnt, [r.zmax for r in reqs])
+            cnts = self.d_cnt[: len(reqs)].to("cpu", non_blocking=False).numpy()
+            lists = []
+            for i in range(len(reqs)):   # only the entries each trial filled
+                keep = min(int(cnts[i]), M)
+                lists.append(self.d_out[i * M * 16: (i * M + keep) * 16].to("cpu").numpy())
+        done = time.perf_counter()
+        out = []
+        for i, r in enumerate(reqs):
+            c = lists[i].view(fdas.CAND_DTYPE).copy()
+            c.sort(order=["h", "r_top", "z_idx"])
+            out.append(Result(c, int(cnts[i]), r.zmax, ns[i], r.arrival, done, len(reqs)))
+        return out
 
     def release(self):
-        for z, b in self.batches.items():
-            fdas.fdas_batch_destroy(b)
-            self.s._release(self.bytes[z])
-        self.batches.clear()
+        if self.batch is not None:
+            fdas.fdas_batch_destroy(self.batch)
+            self.batch = None

@@ -107,10 +107,12 @@ def test_newer_entry_points_reject_null_and_bad_arguments(lib):
     assert so.fdas_plan_set_whitening(None, 1) == INV
     assert so.fdas_plan_set_harmsum_block(None, 32) == INV
     assert so.fdas_plan_set_interbin(None, 1) == INV
+    assert so.fdas_plan_set_wait_limit(None, 1) == INV
     assert so.fdas_distill(None, None, None, None, None) == INV
     assert so.fdas_batch_set_graphs(None, 1) == INV
     assert so.fdas_batch_get_info(None, None) == INV
-    assert so.fdas_search_batch(None, None, None, 1, None, None) == INV
+    assert so.fdas_search_batch(None, None, None, None, 1, None, None) == INV
+    assert so.fdas_batch_add_class(None, 100, 256, 4096) == INV
     assert so.fdas_batch_destroy(None) == lib.FDAS_OK
     out = ctypes.c_void_p()
     assert so.fdas_batch_create_tuned(None, 1 << 14, 20, 2, 64, 4, 6.0, 16, None, None) == INV
@@ -128,7 +130,24 @@ def test_binding_dtypes_match_the_c_structs(lib):
     assert lib.PEAK_DTYPE.itemsize == 24
     assert list(lib.PEAK_DTYPE.names) == ["r_top", "z_idx", "h", "power", "sigma", "log10_p"]
     import ctypes
-    assert ctypes.sizeof(lib.fdas_batch_info) == 8 + 4 * 4 + 8 * 2 + 4 + 3 * 4 * 8 + 4
+    assert ctypes.sizeof(lib.fdas_batch_info) == 8 + 4 * 4 + 8 * 2 + 4 + 3 * 4 * 8 + 4 + 8
     src = open(os.path.join(ROOT, "include", "fdas.h")).read()
     for field in ("r_top", "z_idx", "power", "sigma", "log10_p", "graph_builds", "tuned_ms"):
         assert field in src
+
+
+def test_misaligned_device_pointers_are_rejected_before_device_work(lib):
+    """A series or spectrum pointer that is not 8-byte aligned (a view at an
+    odd float) is an argument error, returned before the GPU is touched (so
+    it also holds on this machine without one)."""
+    with pytest.raises(lib.FdasError) as e:
+        lib.fdas_spectrum_noalloc(0x10004, 1 << 12, 0x20000, 0)
+    assert e.value.status == lib.FDAS_ERR_INVALID
+    assert "d_series" in str(e.value) and "aligned" in str(e.value)
+    with pytest.raises(lib.FdasError) as e:
+        lib.fdas_spectrum_noalloc(0x10000, 1 << 12, 0x20004, 0)
+    assert e.value.status == lib.FDAS_ERR_INVALID
+    assert "d_spectrum" in str(e.value)
+    so = lib.load()
+    assert so.fdas_batch_create_tuned(None, 1 << 14, 20, 2, 64, 4, 6.0, 16, 0x10004,
+                                      None) == lib.FDAS_ERR_INVALID

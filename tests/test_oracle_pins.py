@@ -483,3 +483,99 @@ def test_thresholds_golden_table():
     T = O.thresholds(16, 6.0)
     for h, v in g["T"].items():
         assert abs(T[int(h)] - v) < 1e-9
+
+
+# ------------------------------------------- windowed sums, cells, candidates --
+def _brute_H(P, h, j, r):
+    """H_h(r, j) by explicit loops over k with the rounding rules spelled out
+    in real arithmetic (round half up in r, half away from zero in jc)."""
+    Z = P.shape[0]
+    zc = (Z - 1) // 2
+    s = 0.0
+    for k in range(1, h + 1):
+        rr = math.floor(k * r / h + 0.5)
+        x = k * (j - zc) / h
+        jj = zc + int(math.copysign(math.floor(abs(x) + 0.5), x))
+        s += P[jj, rr]
+    return s
+
+
+def _small_whitened(nb, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal(nb) + 1j * rng.standard_normal(nb)) / math.sqrt(2.0)
+
+
+def test_correlate_band_equals_direct_sums_at_both_edges():
+    """A column range of Eq. 1 through a sub-band FFT equals the direct sums
+    sum_d Xw[r+d] tau(d), including ranges that reach past either end of the
+    spectrum (where Xw is zero)."""
+    nb, m = 300, 16
+    Xw = _small_whitened(nb, 11)
+    taus = O.template_bank(6, 2, m)
+    for c0, c1 in ((0, 40), (5, 6), (130, 171), (270, 300), (0, 300)):
+        for j in (0, 3, 6):
+            got = np.abs(O.correlate_band(Xw, taus[j], c0, c1)) ** 2
+            ref = O.plane_cells(Xw, taus, np.full(c1 - c0, j), np.arange(c0, c1))
+            assert np.max(np.abs(got - ref)) <= 1e-12 * max(1.0, ref.max())
+
+
+def test_harmonic_sums_window_equals_whole_plane_sums():
+    """Windowed sums (the plane formed only at the columns each ratio k/h
+    reads) equal the whole-plane sums restricted to the window, at the start,
+    in the middle and at the end of the spectrum, for every level."""
+    nb, m, zmax = 700, 16, 8
+    Xw = _small_whitened(nb, 12)
+    taus = O.template_bank(zmax, 2, m)
+    H = O.harmonic_sums(O.power_plane(Xw, taus), 16)
+    for r_a, r_b in ((0, 37), (301, 420), (650, 700)):
+        Hw = O.harmonic_sums_window(Xw, taus, 16, r_a, r_b)
+        assert sorted(Hw) == [1, 2, 4, 8, 16]
+        for h in Hw:
+            assert np.max(np.abs(Hw[h] - H[h][:, r_a:r_b])) <= 1e-10 * H[h].max()
+
+
+def test_harmonic_sum_cells_equals_brute_force():
+    """harmonic_sum_cells (direct Eq. 1 cell sums) against the loop-defined
+    H_h on the whole oracle plane, at random cells including both z edges
+    and the lowest bins; (j, r) swapped anywhere would fail it."""
+    nb, m, zmax = 400, 16, 10
+    Xw = _small_whitened(nb, 13)
+    taus = O.template_bank(zmax, 2, m)
+    P = O.power_plane(Xw, taus)
+    Z = taus.shape[0]
+    rng = np.random.default_rng(5)
+    js = np.concatenate([[0, Z - 1, 2, Z - 3], rng.integers(0, Z, 40)])
+    rs = np.concatenate([[1, 399, 3, 17], rng.integers(1, nb, 40)])
+    got = O.harmonic_sum_cells(Xw, taus, 16, js, rs)
+    for h in (1, 2, 4, 8, 16):
+        ref = np.array([_brute_H(P, h, j, r) for j, r in zip(js, rs)])
+        assert np.max(np.abs(got[h] - ref)) <= 1e-10 * max(1.0, ref.max()), h
+
+
+def test_candidates_equal_brute_force_list():
+    """candidates() against an explicit loop over h, then r >= 1, then j,
+    that keeps (r, j, h, H) with H >= T_h: the same rows in the same order.
+    At sigma = 1 the thresholds are low enough for many rows at every level;
+    planted cells put H exactly on T_1 (kept) and one float below (dropped),
+    and a large bin-0 column checks that r = 0 is never a candidate."""
+    rng = np.random.default_rng(9)
+    Z, nb = 9, 160
+    P = rng.exponential(size=(Z, nb))
+    T = O.thresholds(16, 1.0)
+    P[:, 0] = 50.0
+    P[2, 40] = T[1]
+    P[3, 41] = np.nextafter(T[1], 0.0)
+    rows, H = O.candidates(P, 16, 1.0)
+    want = []
+    for h in (1, 2, 4, 8, 16):
+        for r in range(1, nb):
+            for j in range(Z):
+                v = _brute_H(P, h, j, r)
+                if v >= T[h]:
+                    want.append((r, j, h, v))
+    assert [(a, b, c) for a, b, c, _ in rows] == [(a, b, c) for a, b, c, _ in want]
+    assert np.allclose([v for *_, v in rows], [v for *_, v in want], rtol=1e-12, atol=0)
+    keys = {(a, b, c) for a, b, c, _ in rows}
+    assert (40, 2, 1) in keys and (41, 3, 1) not in keys
+    assert all(r >= 1 for r, *_ in rows)
+    assert {c for _, _, c, _ in rows} == {1, 2, 4, 8, 16}
