@@ -51,7 +51,7 @@ def test_noalloc_spectrum_matches_plan_path(gpu_lib, logn):
 def test_noalloc_rejects_sizes_beyond_its_limit(gpu_lib):
     fd = gpu_lib
     with pytest.raises(fd.FdasError) as e:
-        fd.fdas_spectrum_noalloc(1, 1 << 21, 1, 0)
+        fd.fdas_spectrum_noalloc(256, 1 << 21, 256, 0)   # aligned stand-ins: never touched
     assert e.value.status == fd.FDAS_ERR_INVALID
     assert "2^20" in str(e.value)
 
