@@ -387,10 +387,6 @@ int bank_natural_launch(fdas_plan* p, float2* out) {
 }  // namespace
 
 int launch_bank_natural(fdas_plan* p, float2* d_out) {
-  if (uses_corr16(p))  // already in natural order
-    return cuda_check(cudaMemcpyAsync(d_out, p->bank, sizeof(float2) * (size_t)p->Z * p->L,
-                                      cudaMemcpyDeviceToDevice, p->stream),
-                      "copy bank");
   switch (p->L) {
     case 2048: return bank_natural_launch<2048>(p, d_out);
     case 4096: return bank_natural_launch<4096>(p, d_out);
@@ -400,7 +396,6 @@ int launch_bank_natural(fdas_plan* p, float2* d_out) {
 }
 
 int launch_segments(fdas_plan* p, const float2* d_white) {
-  if (uses_corr16(p)) return launch_segments16(p, d_white);
   switch (p->L) {
     case 2048: return seg_launch<2048>(p, d_white);
     case 4096: return seg_launch<4096>(p, d_white);
@@ -411,7 +406,6 @@ int launch_segments(fdas_plan* p, const float2* d_white) {
 
 int launch_correlate(fdas_plan* p, float* d_plane, float* d_q4, fdas_cand* d_cands,
                      unsigned long long* d_count) {
-  if (uses_corr16(p)) return launch_correlate16(p, d_plane, d_q4, d_cands, d_count);
   switch (p->L) {
     case 2048:
       return p->interbin ? corr_launch<2048, 1>(p, d_plane, d_q4, d_cands, d_count)

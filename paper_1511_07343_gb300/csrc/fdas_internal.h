@@ -140,19 +140,6 @@ bool split_235(int64_t M, int* M1, int* M2);
 int launch_whiten(fdas_plan* p, const float2* d_spec, float2* d_white);
 int launch_whiten_block(fdas_plan* p, const float2* d_spec, float2* d_white);
 
-// Segments of 8192 bins use the 16-points-per-thread correlation
-// (fdas_correlate16.cu), whose template and segment spectra are stored in
-// natural order; shorter segments use the packed layout of fdas_correlate.cu.
-#ifndef FDAS_CORR16
-#define FDAS_CORR16 1
-#endif
-inline bool uses_corr16(const fdas_plan* p) { return FDAS_CORR16 && p->L == 8192; }
-
-// fdas_correlate16.cu
-int launch_segments16(fdas_plan* p, const float2* d_white);
-int launch_correlate16(fdas_plan* p, float* d_plane, float* d_q4, fdas_cand* d_cands,
-                       unsigned long long* d_count);
-
 // fdas_correlate.cu
 int launch_segments(fdas_plan* p, const float2* d_white);
 int launch_bank_natural(fdas_plan* p, float2* d_out);

@@ -177,7 +177,7 @@ __global__ void k_template_taps(double2* __restrict__ taps, int Z, int m, int zm
 // bank[j][k] = (1/L) sum_i taps[j][i] exp(+2 pi i k (i - m/2) / L), float64
 // accumulation, rotation by recurrence re-seeded every 32 taps.
 __global__ void k_template_bank(const double2* __restrict__ taps, float2* __restrict__ bank,
-                                int m, int L, int natural) {
+                                int m, int L) {
   extern __shared__ double2 s_taps[];
   const int j = blockIdx.y;
   for (int i = threadIdx.x; i < m; i += blockDim.x) s_taps[i] = taps[(size_t)j * m + i];
@@ -201,10 +201,6 @@ __global__ void k_template_bank(const double2* __restrict__ taps, float2* __rest
     w = w * step;
   }
   const double inv = 1.0 / (double)L;
-  if (natural) {  // bank[j][k] (the 8192-bin correlation)
-    bank[(size_t)j * L + k] = make_float2((float)(acc.re * inv), (float)(acc.im * inv));
-    return;
-  }
   // packed layout: slot ((k2 / RA2) RA2 + k2 % RA2) 16 + u holds
   // (re[2u], re[2u+1], im[2u], im[2u+1]) with k = (2u + e) + 32 k2
   const int RA2 = L / 512;
@@ -243,8 +239,7 @@ int launch_template_taps(fdas_plan* p) {
 int launch_template_bank(fdas_plan* p) {
   dim3 grid((p->L + 127) / 128, p->Z);
   const size_t smem = sizeof(double2) * p->m;
-  k_template_bank<<<grid, 128, smem, p->stream>>>(p->taps, p->bank, p->m, p->L,
-                                                  uses_corr16(p) ? 1 : 0);
+  k_template_bank<<<grid, 128, smem, p->stream>>>(p->taps, p->bank, p->m, p->L);
   return cuda_check(cudaGetLastError(), "k_template_bank");
 }
 
@@ -255,8 +250,7 @@ int launch_template_interbin(fdas_plan* p) {
   if (rc) return rc;
   dim3 grid((p->L + 127) / 128, 2 * p->Z);
   const size_t smem = sizeof(double2) * p->m;
-  k_template_bank<<<grid, 128, smem, p->stream>>>(p->taps_ib, p->bank_ib, p->m, p->L,
-                                                  uses_corr16(p) ? 1 : 0);
+  k_template_bank<<<grid, 128, smem, p->stream>>>(p->taps_ib, p->bank_ib, p->m, p->L);
   return cuda_check(cudaGetLastError(), "k_template_bank (half-bin)");
 }
 
