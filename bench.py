@@ -41,9 +41,11 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch at the benchmark size, from an ncu
 # counter capture of the kernel, each valid only for the kernel source it was
 # taken with (sha256 prefix of the file); None once that source changes.
+# (A 2^21-sample capture, one launch per kernel, scaled to the 2^23-sample
+# launch by the (segment, template) pairs or top bins it processes.)
 MEASURED_TRAFFIC = {
-    "k_correlate_fused": (4.408e+09, "paper_1511_07343_gb300/csrc/fdas_correlate.cu", "ea53cf3cd8a00fbc"),
-    "k_harmsum_staged": (8.473e+08, "paper_1511_07343_gb300/csrc/fdas_harmsum.cu", "35745edd7841abeb"),
+    "k_correlate_fused": (4.110e+09, "paper_1511_07343_gb300/csrc/fdas_correlate.cu", "ea53cf3cd8a00fbc"),
+    "k_harmsum_staged": (8.470e+08, "paper_1511_07343_gb300/csrc/fdas_harmsum.cu", "a966e439669c6f55"),
 }
 
 

@@ -83,7 +83,8 @@ struct Corr {
   static constexpr int NCOLS = 128 * NGROUPS;   // per thread: 64 (F) + 64 (B twiddles)
   static constexpr int MAXCTA = 512 / NCOLS;
   static constexpr int MINB = L == 8192 ? 2 : 4;
-  static constexpr size_t SMEM = 16 * (size_t)(XF4 + RA2 * 17) + 4 * (size_t)L;
+  // exchange buffer, A1 twiddles, power row (L floats), 4-bin maxima row (L/4)
+  static constexpr size_t SMEM = 16 * (size_t)(XF4 + RA2 * 17) + 4 * (size_t)L + (size_t)L;
 };
 
 // Exchange-buffer slot of row r, packed pair u: 16 float4 per row, the pair
@@ -93,6 +94,20 @@ struct Corr {
 // (A2 -> B): A2 thread (u, c) reads rows {16 a + c} and writes its outputs d
 // into rows {16 d + c}, the same slots, so it needs no barrier in between.
 FDAS_DEV int xsw(int r, int u) { return r * 16 + (u ^ (r & 7)); }
+
+// Bulk copy (TMA engine, no tensor map) of `bytes` from shared to global
+// memory; both addresses 16-byte aligned, bytes a multiple of 16.
+FDAS_DEV void bulk_s2g(void* gdst, const void* ssrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+               "r"((uint32_t)__cvta_generic_to_shared(ssrc)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+FDAS_DEV void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+FDAS_DEV void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+FDAS_DEV void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 
 FDAS_DEV c2 c2_of(float4 v) { return c2{make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
 FDAS_DEV float4 f4_of(c2 v) { return make_float4(v.re.x, v.re.y, v.im.x, v.im.y); }
@@ -113,7 +128,24 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
   // warp reads two rows a at once, which the padding puts on other banks
   float4* twA = smem4 + C::XF4;
   float* Ps = reinterpret_cast<float*>(twA + RA2 * 17);
+  float* Q4s = Ps + L;  // 4-bin maxima of the row slice (bulk path)
   __shared__ uint32_t s_tmem;
+  // Integer-bin planes with m % 16 == 0 leave the kernel by bulk copies: the
+  // valid slice of the power row (Ps + m/2, 4 nvalid bytes) and its 4-bin
+  // maxima (Q4s, nvalid bytes), both 16-byte aligned at either end. Thread 0
+  // issues the copies of pair p after the first CTA barrier of pair p + 1
+  // (every thread has fenced its shared-memory writes of pair p before it)
+  // and waits until they have read shared memory before the second one,
+  // after which pair p + 1 rewrites Ps and Q4s.
+  const bool bulk = IB == 0 && (m % 16) == 0;
+  auto issue_bulk = [&](int64_t pp) {  // pair pp's row slice (thread 0)
+    const int ps = (int)(pp / Z);
+    const int pz = (int)(pp - (int64_t)ps * Z);
+    const int64_t pr0 = (int64_t)ps * V;
+    const uint32_t nv = (uint32_t)min((int64_t)V, nb - pr0);
+    if (plane) bulk_s2g(plane + (size_t)pz * nb + pr0, Ps + m / 2, 4 * nv);
+    if (q4) bulk_s2g(q4 + (size_t)pz * (nb >> 2) + (pr0 >> 2), Q4s, nv);
+  };
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int e = tid; e < RA2 * 16; e += T) {
     const float2 w = cconj(__ldg(twL + (((e >> 4) * (e & 15) * 32) & (L - 1))));
@@ -201,6 +233,7 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
 #pragma unroll
     for (int c = 0; c < 16; ++c) X[xsw(a1 * 16 + c, u1)] = f4_of(v[brev<16>(c)]);
     __syncthreads();
+    if (bulk && tid == 0 && p > p0) issue_bulk(p - 1);  // the previous pair's row slice
     // ---- A2
     c2 w[NB2][RA2];
 #pragma unroll
@@ -229,6 +262,8 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
         }
       }
     }
+    // the copies of the previous pair's row slice have read Ps and Q4s
+    if (bulk && tid == 0 && p > p0) bulk_wait_read();
     __syncthreads();
     // ---- B
     c2 y[16];
@@ -266,7 +301,9 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
         const float4 p4 = P4[n >> 2];
         const int k = (n - half_m) >> 2;  // float4 index in the row slice
         const float mx = fmaxf(fmaxf(p4.x, p4.y), fmaxf(p4.z, p4.w));
-        if (prow) {
+        if (bulk) {
+          Q4s[k] = mx;  // the plane row itself leaves from Ps
+        } else if (prow) {
           if constexpr (IB) {
             prow[8 * k] = p4.x;
             prow[8 * k + 2] = p4.y;
@@ -276,7 +313,7 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
             reinterpret_cast<float4*>(prow)[k] = p4;
           }
         }
-        if (qrow) qrow[k] = mx;
+        if (qrow && !bulk) qrow[k] = mx;
         hit |= mx >= thr1;
       }
     }
@@ -294,6 +331,15 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
         emit(in && p4.z >= thr1, rk + 2, z, 1, p4.z, cands, count, maxc);
         emit(in && p4.w >= thr1, rk + 3, z, 1, p4.w, cands, count, maxc);
       }
+    }
+    // this thread's Ps and Q4s writes, visible to the bulk copies
+    if (bulk) fence_proxy_async_shared();
+  }
+  if (bulk) {  // the last pair's row slice
+    __syncthreads();
+    if (tid == 0 && p1 > p0) {
+      issue_bulk(p1 - 1);
+      bulk_wait_all();
     }
   }
   tmem_fence_before_sync();
