@@ -101,10 +101,11 @@ int fdas_plan_get_info(const fdas_plan* plan, fdas_plan_info* info);
  * sorted by (h, r_top, z_idx); h_counts[t] is the exact number found, which
  * may exceed max_cands: then only max_cands are stored and the call returns
  * FDAS_ERR_OVERFLOW after finishing every trial. Synchronises the stream.
- * With n_trials > 1 on a stream other than the legacy default stream, trial
- * t-1's candidates are read back and sorted while trial t runs (a second
- * candidate list alternates with the first: the second trial lane's, see
- * below, or one allocated on first use). */
+ * With n_trials > 1 on a stream other than the legacy default stream, earlier
+ * trials' candidates are read back and sorted while later trials run: with
+ * the second trial lane (below) trial t-2 while trials t-1 and t run, through
+ * four candidate lists (the plan's, the lane's and two allocated on first
+ * use); without it trial t-1 while trial t runs, through two. */
 int fdas_search(fdas_plan* plan, const float* d_series, int32_t n_trials,
                 fdas_cand* h_out, int64_t* h_counts);
 
@@ -117,7 +118,9 @@ int fdas_search(fdas_plan* plan, const float* d_series, int32_t n_trials,
  * copies to overlap. With the second trial lane (below) the series go
  * through four staging buffers (the plan's, the lane's and two allocated on
  * the first such call, 8N bytes), so the copy of trial t+1 never waits for
- * a running trial; where no lane is used (tensor-core or half-bin modes)
+ * a running trial, and the candidates through four lists (two more allocated
+ * then, 32 max_cands + 16 bytes), so trial t-2 is read back while trials
+ * t-1 and t run; where no lane is used (tensor-core or half-bin modes)
  * the first such call allocates a second staging buffer and candidate list
  * (4N + 16 max_cands bytes). */
 int fdas_search_host(fdas_plan* plan, const float* h_series, int32_t n_trials,

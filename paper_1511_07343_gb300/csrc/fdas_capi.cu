@@ -94,6 +94,10 @@ void free_plan(fdas_plan* p) {
     if (b) cudaFree(b);
   if (p->cands2) cudaFree(p->cands2);
   if (p->count2) cudaFree(p->count2);
+  for (int e = 0; e < 2; ++e) {
+    if (p->cands3[e]) cudaFree(p->cands3[e]);
+    if (p->count3[e]) cudaFree(p->count3[e]);
+  }
   void* ptrs[] = {p->tw_L, p->tw_M1, p->tw_M2, p->tw4_lo, p->tw4_hi, p->twN_lo, p->twN_hi,
                   p->taps, p->bank, p->series, p->zbuf, p->spec, p->spec2, p->white, p->seg,
                   p->plane, p->q4, p->cands, p->count, p->hs_list, p->hs_nlist,
@@ -286,6 +290,8 @@ int ensure_lane(fdas_plan* p) {
   l->hs_nlist = own.hs_nlist; l->stream = own.stream; l->device_bytes = own.device_bytes;
   l->series2 = nullptr; l->cands2 = nullptr; l->count2 = nullptr; l->cstream = nullptr;
   l->series3[0] = l->series3[1] = nullptr;
+  l->cands3[0] = l->cands3[1] = nullptr;
+  l->count3[0] = l->count3[1] = nullptr;
   for (int k = 0; k < 4; ++k) l->ev_in[k] = l->ev_done[k] = nullptr;
   l->lane = nullptr; l->ev_fork = l->ev_join = nullptr;
   l->dkeys = nullptr; l->dvals = nullptr; l->dbits = 0;
@@ -361,9 +367,18 @@ int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_ca
   if (lanes && !d_series)
     for (int e = 0; e < 2; ++e)
       if (!p->series3[e] && (rc = dalloc(p, &p->series3[e], (size_t)p->N))) return rc;
+  if (lanes)
+    for (int e = 0; e < 2; ++e) {
+      if (!p->cands3[e] && (rc = dalloc(p, &p->cands3[e], (size_t)p->max_cands))) return rc;
+      if (!p->count3[e] && (rc = dalloc(p, &p->count3[e], 1))) return rc;
+    }
   float* buf[4] = {p->series, lanes ? q[1]->series : p->series2, p->series3[0], p->series3[1]};
-  fdas_cand* cbuf[2] = {p->cands, lanes ? q[1]->cands : p->cands2};
-  unsigned long long* nbuf[2] = {p->count, lanes ? q[1]->count : p->count2};
+  // candidate list of trial t: cbuf[t % K] (with lanes, t mod 4: the read-back
+  // of trial t - 2 overlaps trials t - 1 and t; without, t mod 2)
+  fdas_cand* cbuf[4] = {p->cands, lanes ? q[1]->cands : p->cands2, p->cands3[0], p->cands3[1]};
+  unsigned long long* nbuf[4] = {p->count, lanes ? q[1]->count : p->count2, p->count3[0],
+                                 p->count3[1]};
+  const int D = lanes ? 2 : 1;  // trials enqueued ahead of the one read back
   if (lanes) {  // the lane starts after the caller's work on the plan stream
     rc = cuda_check(cudaEventRecord(p->ev_fork, p->stream), "event");
     if (!rc) rc = cuda_check(cudaStreamWaitEvent(q[1]->stream, p->ev_fork, 0), "wait");
@@ -373,7 +388,7 @@ int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_ca
   bool overflow = false;
   // read back and sort trial t (its kernels are done once ev_done fires)
   auto finish = [&](int32_t t) -> int {
-    const int b = t & 1;
+    const int b = t % K;
     int r = cuda_check(cudaEventSynchronize(p->ev_done[t % K]), "trial done");
     unsigned long long cnt = 0;
     if (!r)
@@ -403,9 +418,9 @@ int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_ca
   for (int32_t t = 0; t < n_trials && !rc; ++t) {
     const int b = t & 1, k = t % K;
     if (d_series) {
-      rc = run_trial(q[b], d_series + (size_t)t * p->N, cbuf[b], nbuf[b]);
+      rc = run_trial(q[b], d_series + (size_t)t * p->N, cbuf[k], nbuf[k]);
       if (!rc) rc = cuda_check(cudaEventRecord(p->ev_done[k], q[b]->stream), "event");
-      if (!rc && t >= 1) rc = finish(t - 1);
+      if (!rc && t >= D) rc = finish(t - D);
       continue;
     }
     if (t + 1 < n_trials) {
@@ -419,13 +434,13 @@ int host_pipeline(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_ca
       if (!rc) rc = cuda_check(cudaEventRecord(p->ev_in[k1], p->cstream), "event");
     }
     if (!rc) rc = cuda_check(cudaStreamWaitEvent(q[b]->stream, p->ev_in[k], 0), "wait");
-    if (!rc) rc = run_trial(q[b], buf[k], cbuf[b], nbuf[b]);
+    if (!rc) rc = run_trial(q[b], buf[k], cbuf[k], nbuf[k]);
     if (!rc) rc = cuda_check(cudaEventRecord(p->ev_done[k], q[b]->stream), "event");
-    // the host reads back trial t-1 while trial t runs; trial t+1 reuses
-    // its lane's candidate list only after this returns
-    if (!rc && t >= 1) rc = finish(t - 1);
+    // the host reads back trial t - D while the trials after it run; the
+    // next trial to use its candidate list is enqueued only after this returns
+    if (!rc && t >= D) rc = finish(t - D);
   }
-  if (!rc && n_trials >= 1) rc = finish(n_trials - 1);
+  for (int32_t t = std::max(0, n_trials - D); t < n_trials && !rc; ++t) rc = finish(t);
   if (!rc && lanes) {  // the plan stream continues after the lane's work
     rc = cuda_check(cudaEventRecord(p->ev_join, q[1]->stream), "event");
     if (!rc) rc = cuda_check(cudaStreamWaitEvent(p->stream, p->ev_join, 0), "wait");
@@ -873,6 +888,8 @@ fdas_plan* unowned_copy(const fdas_plan* b) {
   v->lane_gen = 0;
   v->series2 = nullptr; v->series3[0] = v->series3[1] = nullptr;
   v->cands2 = nullptr; v->count2 = nullptr; v->cstream = nullptr;
+  v->cands3[0] = v->cands3[1] = nullptr;
+  v->count3[0] = v->count3[1] = nullptr;
   for (int k = 0; k < 4; ++k) v->ev_in[k] = v->ev_done[k] = nullptr;
   v->dkeys = nullptr; v->dvals = nullptr; v->dbits = 0;
   v->gbank = nullptr; v->gstatus = nullptr; v->taps_ib = nullptr; v->bank_ib = nullptr;

@@ -82,6 +82,11 @@ struct fdas_plan {
   float* series3[2] = {nullptr, nullptr};
   fdas_cand* cands2 = nullptr;
   unsigned long long* count2 = nullptr;
+  // with the trial lane, two more candidate lists and counts (trial t writes
+  // list t mod 4), so that the host reads trial t - 2 back while trials t - 1
+  // and t run
+  fdas_cand* cands3[2] = {nullptr, nullptr};
+  unsigned long long* count3[2] = {nullptr, nullptr};
   cudaStream_t cstream = nullptr;
   cudaEvent_t ev_in[4] = {nullptr, nullptr, nullptr, nullptr};    // series copy landed in slot k
   cudaEvent_t ev_done[4] = {nullptr, nullptr, nullptr, nullptr};  // the trial reading slot k finished
