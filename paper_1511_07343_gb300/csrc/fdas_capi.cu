@@ -71,6 +71,7 @@ int dalloc(fdas_plan* p, T** ptr, size_t count) {
   const size_t bytes = count * sizeof(T);
   cudaError_t e = cudaMalloc((void**)ptr, bytes);
   if (e != cudaSuccess) {
+    cudaGetLastError();  // a refused allocation must not surface at a later launch check
     *ptr = nullptr;
     return set_error(FDAS_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
                                          cudaGetErrorString(e));
@@ -113,6 +114,7 @@ int launch_plane(fdas_plan* p, float* d_plane, float* d_q4, fdas_cand* d_out,
 
 // The path for one trial; the plane goes to p->plane, candidates to d_out.
 int run_trial(fdas_plan* p, const float* d_x, fdas_cand* d_out, unsigned long long* d_count) {
+  NvtxRange range("fdas trial");
   int rc;
   p->last_on_lane = false;
   if ((rc = cuda_check(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), p->stream),
@@ -465,6 +467,7 @@ extern "C" {
 
 int fdas_plan_create(fdas_plan** out, int64_t N, int32_t zmax, int32_t dz, int32_t m,
                      int32_t L, int32_t nharm, float sigma, int64_t max_cands, void* stream) {
+  NvtxRange range("fdas_plan_create");
   if (!out) return set_error(FDAS_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (zmax < 0 || dz <= 0 || zmax % dz != 0)
@@ -572,6 +575,7 @@ int fdas_plan_get_info(const fdas_plan* p, fdas_plan_info* info) {
 
 int fdas_search(fdas_plan* p, const float* d_series, int32_t n_trials, fdas_cand* h_out,
                 int64_t* h_counts) {
+  NvtxRange range("fdas_search");
   if (!p || !d_series || n_trials < 0 || (n_trials > 0 && (!h_out || !h_counts)))
     return set_error(FDAS_ERR_INVALID, "bad argument to fdas_search");
   if (int rc = check_aligned(d_series, 8, "d_series")) return rc;
@@ -582,6 +586,7 @@ int fdas_search(fdas_plan* p, const float* d_series, int32_t n_trials, fdas_cand
 
 int fdas_search_host(fdas_plan* p, const float* h_series, int32_t n_trials, fdas_cand* h_out,
                      int64_t* h_counts) {
+  NvtxRange range("fdas_search_host");
   if (!p || !h_series || n_trials < 0 || (n_trials > 0 && (!h_out || !h_counts)))
     return set_error(FDAS_ERR_INVALID, "bad argument to fdas_search_host");
   if (n_trials == 1 || p->stream == nullptr) {
@@ -605,6 +610,7 @@ int fdas_search_host(fdas_plan* p, const float* h_series, int32_t n_trials, fdas
 
 int fdas_search_device(fdas_plan* p, const float* d_series, int32_t n_trials, fdas_cand* d_out,
                        int64_t* d_counts) {
+  NvtxRange range("fdas_search_device");
   if (!p || !d_series || n_trials < 0 || (n_trials > 0 && (!d_out || !d_counts)))
     return set_error(FDAS_ERR_INVALID, "bad argument to fdas_search_device");
   if (int rc = check_aligned(d_series, 8, "d_series")) return rc;
@@ -1129,7 +1135,10 @@ int fdas_batch_create_tuned(fdas_batch** out, int64_t N_max, int32_t zmax, int32
     if (N_max < (1 << 12) || N_max > (1 << 24))
       return set_error(FDAS_ERR_INVALID, "N must be 2^a 3^b 5^c with a >= 12 and 2^12 <= N <= 2^24");
     cudaError_t e = cudaMalloc((void**)&own, sizeof(float) * (size_t)N_max);
-    if (e != cudaSuccess) return set_error(FDAS_ERR_NOMEM, "probe series allocation failed");
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(FDAS_ERR_NOMEM, "probe series allocation failed");
+    }
     rc = launch_probe_noise(own, N_max, 0x5eedull, s);
     d_probe = own;
   }
@@ -1211,6 +1220,7 @@ int fdas_batch_destroy(fdas_batch* b) {
 int fdas_search_batch(fdas_batch* b, const float* const* d_series, const int64_t* N,
                       const int32_t* zmax, int32_t n_trials, fdas_cand* d_out,
                       int64_t* d_counts) {
+  NvtxRange range("fdas_search_batch");
   if (!b || !d_series || !N || n_trials < 0 || (n_trials > 0 && (!d_out || !d_counts)))
     return set_error(FDAS_ERR_INVALID, "bad argument to fdas_search_batch");
   if (n_trials > 0) {

@@ -201,6 +201,7 @@ int launch_distill(fdas_plan* p, const fdas_cand* d_cands, const int64_t* d_coun
     const size_t n = (size_t)1 << bits;
     if (cudaMalloc((void**)&p->dkeys, n * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc((void**)&p->dvals, n * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();  // a refused allocation must not surface at a later launch check
       if (p->dkeys) cudaFree(p->dkeys);
       p->dkeys = nullptr;
       p->dvals = nullptr;

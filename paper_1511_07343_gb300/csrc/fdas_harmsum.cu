@@ -430,7 +430,10 @@ int make_hs_order(fdas_plan* p) {
     });
     uint32_t* d = nullptr;
     cudaError_t e = cudaMalloc((void**)&d, sizeof(uint32_t) * (size_t)n);
-    if (e != cudaSuccess) return set_error(FDAS_ERR_NOMEM, "tile order table");
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(FDAS_ERR_NOMEM, "tile order table");
+    }
     p->hs_order[k] = d;
     p->device_bytes += (int64_t)sizeof(uint32_t) * n;
     e = cudaMemcpy(d, ord.data(), sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -113,6 +114,15 @@ constexpr int64_t kHsListCap = (int64_t)1 << 20;
 
 // plane columns: nb, or 2 nb (half bins) for half-bin planes
 inline int64_t plane_width(const fdas_plan* p) { return p->nb << p->interbin; }
+
+// NVTX range for the lifetime of a scope (host side: what the entry points
+// enqueue); a no-op unless a profiler or tracer is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // error plumbing
 int set_error(int code, const std::string& msg);

@@ -123,7 +123,7 @@ class Server:
         self._lock = threading.Lock()
         self._queue: "queue.Queue[_Request | None]" = queue.Queue()
         self.stats = {"slots": n_fit, "admitted": 0, "batches": 0, "cancelled": 0,
-                      "largest_batch": 0}
+                      "largest_batch": 0, "hbm_reserved": n_fit * self.slot_bytes}
         self._slots = []
         self._closed = False
         try:

@@ -165,3 +165,33 @@ def test_misaligned_pointers_are_argument_errors(gpu_lib):
         torch.cuda.synchronize()
     finally:
         fd.fdas_plan_destroy(plan)
+
+
+def test_allocation_refusal_is_nomem_and_leaks_nothing(gpu_lib):
+    """A plan larger than the device (a 2^24-sample plane of 10001 templates,
+    336 GB) is refused with FDAS_ERR_NOMEM: whatever was allocated before the
+    refusal is freed, and the refused allocation does not surface as an error
+    at a later launch (a small search afterwards works)."""
+    fd = gpu_lib
+    torch.cuda.synchronize()
+    free0, total = torch.cuda.mem_get_info(DEV)
+    zmax = 10000
+    assert (2 * (zmax // 2) + 1) * (1 << 23) * 4 > total
+    with pytest.raises(fd.FdasError) as e:
+        fd.fdas_plan_create(1 << 24, zmax, 2, 512, 8192, 16, 6.0, 1 << 16,
+                            torch.cuda.current_stream(DEV).cuda_stream)
+    assert e.value.status == fd.FDAS_ERR_NOMEM
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(DEV)
+    assert free1 >= free0 - (64 << 20)
+    N = 1 << 14
+    x = make_series(N, 12, [Chirp(2000.0, 4.0, 14.0, 0.0, 2)])
+    plan = plan_on(fd, N, 20, 64, 2048, 4)
+    try:
+        info = fd.fdas_plan_get_info(plan)
+        out = np.zeros(info.max_cands, dtype=fd.CAND_DTYPE)
+        cnt = np.zeros(1, dtype=np.int64)
+        fd.fdas_search(plan, torch.from_numpy(x).to(DEV), 1, out, cnt)
+    finally:
+        fd.fdas_plan_destroy(plan)
+    assert cnt[0] > 0
