@@ -519,3 +519,40 @@ def test_host_pipeline_equals_single_trials(gpu_lib):
     finally:
         fd.fdas_plan_destroy(plan)
     assert all(c > 0 for c, _ in single)
+
+
+@pytest.mark.parametrize("n_trials", [2, 3, 4, 6])
+def test_pipelined_overflow_keeps_exact_counts(gpu_lib, n_trials):
+    """Several host series through the lane pipeline (the read-back of trial
+    t - 2 overlaps trials t - 1 and t) with a candidate list too small for
+    them: the call returns FDAS_ERR_OVERFLOW after every trial, each count is
+    the exact one a roomy plan reports, and each stored entry is one of that
+    trial's candidates."""
+    fd = gpu_lib
+    N = 1 << 14
+    xs = np.stack([make_series(N, 40 + t, [Chirp(2000.0 + 300 * t, 4.0, 20.0, 0.0, 4)])
+                   for t in range(n_trials)])
+    stream = torch.cuda.Stream(DEV)
+    full = []
+    plan = fd.fdas_plan_create(N, 20, 2, 64, 2048, 4, 6.0, 1 << 16, stream.cuda_stream)
+    try:
+        for t in range(n_trials):
+            o = np.zeros(1 << 16, dtype=fd.CAND_DTYPE)
+            c = np.zeros(1, dtype=np.int64)
+            fd.fdas_search_host(plan, np.ascontiguousarray(xs[t]), 1, o, c)
+            full.append((int(c[0]), keys(o[: c[0]])))
+    finally:
+        fd.fdas_plan_destroy(plan)
+    M = 3
+    plan = fd.fdas_plan_create(N, 20, 2, 64, 2048, 4, 6.0, M, stream.cuda_stream)
+    try:
+        out = np.zeros(n_trials * M, dtype=fd.CAND_DTYPE)
+        cnt = np.zeros(n_trials, dtype=np.int64)
+        status = fd.fdas_search_host(plan, np.ascontiguousarray(xs.ravel()), n_trials, out, cnt)
+    finally:
+        fd.fdas_plan_destroy(plan)
+    assert status == fd.FDAS_ERR_OVERFLOW
+    for t in range(n_trials):
+        n_full, k_full = full[t]
+        assert n_full > M and int(cnt[t]) == n_full
+        assert keys(out[t * M: (t + 1) * M]) <= k_full
