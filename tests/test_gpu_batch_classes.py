@@ -138,3 +138,51 @@ def test_batch_class_errors(gpu_lib):
         assert fd.fdas_batch_get_info(batch).n_classes == 2
     finally:
         fd.fdas_batch_destroy(batch)
+
+
+@pytest.mark.slow
+def test_mixed_zmax_batch_full_size(gpu_lib):
+    """The serving shapes at full size: three 2^23-sample trials and one at an
+    uneven length, zmax 50 / 100 / 200 / 200, 16 harmonics, through one
+    fdas_search_batch call on two lanes: each trial's sorted list is byte for
+    byte the list of a single plan of its class."""
+    from synthetic import random_chirps, snap_235
+    fd = gpu_lib
+    maxc = 1 << 20
+    n_full = 1 << 23
+    rng = np.random.default_rng(21)
+    lengths = [n_full, n_full, n_full, snap_235(3.1e6 * 2)]
+    zmaxes = [50, 100, 200, 200]
+    xs = [make_series(n, 7100 + i, random_chirps(rng, 3, n, z), device=DEV)
+          for i, (n, z) in enumerate(zip(lengths, zmaxes))]
+    single = []
+    stream = torch.cuda.current_stream(DEV).cuda_stream
+    for x, z in zip(xs, zmaxes):
+        m, L = CLASSES[z]
+        plan = fd.fdas_plan_create(len(x), z, 2, m, L, 16, 6.0, maxc, stream)
+        try:
+            out = np.zeros(maxc, dtype=fd.CAND_DTYPE)
+            cnt = np.zeros(1, dtype=np.int64)
+            fd.fdas_search(plan, torch.from_numpy(x).to(DEV), 1, out, cnt)
+        finally:
+            fd.fdas_plan_destroy(plan)
+        single.append(sorted_list(out[: cnt[0]]))
+    st = torch.cuda.Stream(DEV)
+    batch = fd.fdas_batch_create(n_full, 200, 2, *CLASSES[200], 16, 6.0, maxc, st.cuda_stream)
+    try:
+        for z in (50, 100):
+            fd.fdas_batch_add_class(batch, z, *CLASSES[z])
+        fd.fdas_batch_set_graphs(batch, 0)
+        d_xs = [torch.from_numpy(x).to(DEV) for x in xs]
+        d_out = torch.empty(len(xs) * maxc * 16, dtype=torch.uint8, device=DEV)
+        d_cnt = torch.zeros(len(xs), dtype=torch.int64, device=DEV)
+        fd.fdas_search_batch(batch, d_xs, lengths, d_out, d_cnt, zmaxes)
+        torch.cuda.synchronize()
+        arr = d_out.cpu().numpy().view(fd.CAND_DTYPE)
+        cnt = d_cnt.cpu().numpy()
+    finally:
+        fd.fdas_batch_destroy(batch)
+    for t in range(len(xs)):
+        assert len(single[t]) > 0
+        got = sorted_list(arr[t * maxc: t * maxc + cnt[t]])
+        assert got.tobytes() == single[t].tobytes(), t
