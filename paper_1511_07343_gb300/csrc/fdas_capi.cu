@@ -923,26 +923,27 @@ int class_index(const fdas_batch* b, int32_t zmax) {
   return -1;
 }
 
-// Grows one of the base plan's workspaces (the stream is idle: the caller
-// synchronised it); the lane and any captured graph are dropped, since they
-// name the old buffers.
+// Replaces one of the base plan's workspaces by a larger one (the stream is
+// idle: the caller synchronised it). The new buffer is allocated before the
+// old one is freed, so a refused allocation leaves the batch as it was.
 template <typename T>
-int grow(fdas_batch* b, T** buf, int64_t* cap, int64_t need, int64_t elem_now) {
-  fdas_plan* base = b->base;
-  if (*cap >= need) return FDAS_OK;
+int replace_buffer(fdas_plan* base, T** buf, int64_t elem_now, int64_t need) {
+  T* fresh = nullptr;
+  int rc = dalloc(base, &fresh, (size_t)need);
+  if (rc) return rc;
   cudaFree(*buf);
   base->device_bytes -= (int64_t)sizeof(T) * elem_now;
-  *buf = nullptr;
-  *cap = 0;
-  int rc = dalloc(base, buf, (size_t)need);
-  if (rc) return rc;
-  *cap = need;
-  free_lane(base);
+  *buf = fresh;
+  return FDAS_OK;
+}
+
+// The lane and any captured graph name the old workspaces: drop them.
+void drop_workspace_users(fdas_batch* b) {
+  free_lane(b->base);
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
-  return FDAS_OK;
 }
 
 // Adds the zmax class (zmax, m, L) to the batch: templates and tables of its
@@ -978,17 +979,24 @@ int add_class(fdas_batch* b, int32_t zmax, int32_t m, int32_t L) {
   if (!rc) rc = launch_template_taps(c);
   if (!rc) rc = launch_template_bank(c);
   if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream), "class templates");
-  if (!rc)
-    rc = grow(b, &base->seg, &base->seg_cap, (int64_t)c->S * L, base->seg_cap);
-  if (!rc) {
-    const int64_t need = (int64_t)c->Z * base->nb;
-    if (base->plane_cap < need) {
-      cudaFree(base->q4);
-      base->device_bytes -= (int64_t)sizeof(float) * (base->plane_cap / 4);
-      base->q4 = nullptr;
-      rc = grow(b, &base->plane, &base->plane_cap, need, base->plane_cap);
-      if (!rc) rc = dalloc(base, &base->q4, (size_t)need / 4);
+  const int64_t seg_need = (int64_t)c->S * L;
+  if (!rc && base->seg_cap < seg_need) {
+    rc = replace_buffer(base, &base->seg, base->seg_cap, seg_need);
+    if (!rc) {
+      base->seg_cap = seg_need;
+      drop_workspace_users(b);
     }
+  }
+  const int64_t plane_need = (int64_t)c->Z * base->nb;
+  if (!rc && base->plane_cap < plane_need) {
+    // the 4-bin maxima first: if the plane is then refused, the larger
+    // maxima buffer still serves the old plane
+    rc = replace_buffer(base, &base->q4, base->plane_cap / 4, plane_need / 4);
+    if (!rc) {
+      drop_workspace_users(b);  // the maxima buffer moved, whatever comes next
+      rc = replace_buffer(base, &base->plane, base->plane_cap, plane_need);
+    }
+    if (!rc) base->plane_cap = plane_need;
   }
   if (rc) {
     free_class(c);
