@@ -709,15 +709,20 @@ int fdas_plan_set_interbin(fdas_plan* p, int32_t enable) {
   }
   const int64_t need = (int64_t)p->Z * 2 * p->nb;
   if (p->plane_cap < need) {
+    // the larger buffers first: a refused allocation leaves the plan as it was
+    float *plane = nullptr, *q4 = nullptr;
+    if ((rc = dalloc(p, &plane, (size_t)need))) return rc;
+    if ((rc = dalloc(p, &q4, (size_t)need / 4))) {
+      cudaFree(plane);
+      p->device_bytes -= (int64_t)sizeof(float) * need;
+      return rc;
+    }
     if ((rc = cuda_check(cudaStreamSynchronize(p->stream), "sync"))) return rc;
     cudaFree(p->plane);
     cudaFree(p->q4);
     p->device_bytes -= (int64_t)sizeof(float) * (p->plane_cap + p->plane_cap / 4);
-    p->plane = nullptr;
-    p->q4 = nullptr;
-    p->plane_cap = 0;
-    if ((rc = dalloc(p, &p->plane, (size_t)need))) return rc;
-    if ((rc = dalloc(p, &p->q4, (size_t)need / 4))) return rc;
+    p->plane = plane;
+    p->q4 = q4;
     p->plane_cap = need;
   }
   p->interbin = 1;
