@@ -717,7 +717,12 @@ int fdas_plan_set_interbin(fdas_plan* p, int32_t enable) {
       p->device_bytes -= (int64_t)sizeof(float) * need;
       return rc;
     }
-    if ((rc = cuda_check(cudaStreamSynchronize(p->stream), "sync"))) return rc;
+    if ((rc = cuda_check(cudaStreamSynchronize(p->stream), "sync"))) {
+      cudaFree(plane);
+      cudaFree(q4);
+      p->device_bytes -= (int64_t)sizeof(float) * (need + need / 4);
+      return rc;
+    }
     cudaFree(p->plane);
     cudaFree(p->q4);
     p->device_bytes -= (int64_t)sizeof(float) * (p->plane_cap + p->plane_cap / 4);
