@@ -96,11 +96,17 @@ struct Corr {
 FDAS_DEV int xsw(int r, int u) { return r * 16 + (u ^ (r & 7)); }
 
 // Bulk copy (TMA engine, no tensor map) of `bytes` from shared to global
-// memory; both addresses 16-byte aligned, bytes a multiple of 16.
+// memory; both addresses 16-byte aligned, bytes a multiple of 16. The lines
+// are marked evict-first in L2: the plane and its maxima stream out to HBM
+// and would otherwise push the template bank and segment spectra, which
+// every pair re-reads, out of L2 (measured: the correlation 2.28 -> 2.07 ms).
 FDAS_DEV void bulk_s2g(void* gdst, const void* ssrc, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
-               "r"((uint32_t)__cvta_generic_to_shared(ssrc)), "r"(bytes)
-               : "memory");
+  uint64_t policy;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+  asm volatile(
+      "cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(gdst),
+      "r"((uint32_t)__cvta_generic_to_shared(ssrc)), "r"(bytes), "l"(policy)
+      : "memory");
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 FDAS_DEV void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
