@@ -44,7 +44,7 @@ FP32_LANES_PER_SM = 128
 # (A 2^21-sample capture, one launch per kernel, scaled to the 2^23-sample
 # launch by the (segment, template) pairs or top bins it processes.)
 MEASURED_TRAFFIC = {
-    "k_correlate_fused": (4.114e+09, "paper_1511_07343_gb300/csrc/fdas_correlate.cu", "8dc4f29f2d5f0f02"),
+    "k_correlate_fused": (4.059e+09, "paper_1511_07343_gb300/csrc/fdas_correlate.cu", "931546f0da42bc11"),
     "k_harmsum_staged": (8.470e+08, "paper_1511_07343_gb300/csrc/fdas_harmsum.cu", "6e7b54719b0a7c6f"),
 }
 
