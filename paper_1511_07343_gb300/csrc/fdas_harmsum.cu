@@ -102,9 +102,12 @@ constexpr size_t hs_smem() { return (size_t)3 * kStageW * (NT / 32) * sizeof(flo
 
 struct HsCtx {
   float* stage;  // this warp's 3 rotating buffers
-  const float* Q4;
-  int64_t nq, R0w;
-  int lane, zc, sg, ajc;
+  const float* Q4;  // + 4 lane
+  int64_t R0w;
+  // 32-bit row pitch and slice origin (nq <= 2^21 for N <= 2^24): the
+  // per-fraction address work stays in 32-bit uniform registers
+  uint32_t nq, r64;
+  int lane, zc, sg, ajc2;
 };
 
 // copy of the warp's slice of row jz(q) of Q4 (fraction number OI in
@@ -117,12 +120,12 @@ FDAS_DEV void hs_issue(const HsCtx& x) {
     constexpr int q = frac_order(OI);
     constexpr int NC = nchunk(q);
     float* buf = x.stage + (OI % 3) * kStageW;
-    const int row = x.zc + x.sg * ((2 * q * x.ajc + 16) >> 5);
-    const int64_t e_lo = (int64_t)q * (x.R0w >> 6);
+    const int row = x.zc + x.sg * ((q * x.ajc2 + 16) >> 5);
+    const uint32_t e_lo = (uint32_t)q * x.r64;
     // per lane: chunks C = lane + 32 i; the swizzle of chunk C depends on
     // lane only (32 i keeps the row's low bits), so the addresses are a
     // lane base plus compile-time offsets
-    const float* src = x.Q4 + (size_t)row * x.nq + e_lo + 4 * x.lane;
+    const float* src = x.Q4 + ((uint64_t)(uint32_t)row * x.nq + e_lo);
     float* dst = buf + 4 * swz(q, x.lane);
     constexpr int full = NC / 32, rest = NC % 32;
     if (e_lo + 4 * NC <= x.nq) {  // the whole slice lies inside the row
@@ -130,7 +133,7 @@ FDAS_DEV void hs_issue(const HsCtx& x) {
       for (int i = 0; i < full; ++i) cp_async16(dst + 128 * i, src + 128 * i, true);
       if (rest && x.lane < rest) cp_async16(dst + 128 * full, src + 128 * full, true);
     } else {
-      const int64_t lim = x.nq - e_lo - 4 * x.lane;  // this lane's chunk i exists if 128 i < lim
+      const int lim = (int)(x.nq - e_lo) - 4 * x.lane;  // this lane's chunk i exists if 128 i < lim
 #pragma unroll
       for (int i = 0; i < full; ++i) cp_async16(dst + 128 * i, src + 128 * i, 128 * i < lim);
       if (rest && x.lane < rest) cp_async16(dst + 128 * full, src + 128 * full, 128 * full < lim);
@@ -276,13 +279,14 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 32 : 0) k_harmsum_staged(
   const int warp = threadIdx.x >> 5;
   HsCtx x;
   x.stage = stage + warp * 3 * kStageW;
-  x.Q4 = Q4;
-  x.nq = nb >> 2;
-  x.R0w = t * (NT * kHsCells) + (int64_t)kWarpSpan * warp;
   x.lane = threadIdx.x & 31;
+  x.Q4 = Q4 + 4 * x.lane;
+  x.nq = (uint32_t)(nb >> 2);
+  x.R0w = t * (NT * kHsCells) + (int64_t)kWarpSpan * warp;
+  x.r64 = (uint32_t)(x.R0w >> 6);
   x.zc = (Z - 1) / 2;
   const int jc = j - x.zc;
-  x.ajc = jc < 0 ? -jc : jc;
+  x.ajc2 = 2 * (jc < 0 ? -jc : jc);
   x.sg = jc < 0 ? -1 : 1;
   float2 acc[kHsPairs / 2];
   unsigned pmask = 0;
