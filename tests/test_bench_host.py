@@ -141,3 +141,38 @@ def test_candidate_agreement_counts_keys_and_the_threshold_band():
     out = bench.candidate_agreement(a, b, thr)
     assert out == {"common": 2, "only_fused": 2, "only_plain": 2,
                    "only_fused_outside_band": 1, "only_plain_outside_band": 1}
+
+
+def _run_bench(args, env_extra=None, timeout=900):
+    import subprocess
+    import sys
+    env = dict(os.environ, **(env_extra or {}))
+    return subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py")] + args,
+                          capture_output=True, text=True, timeout=timeout, env=env,
+                          cwd=bench.ROOT)
+
+
+def test_reference_arm_prints_one_line_of_the_contract():
+    """`bench.py --impl reference` times the oracle on the host cores (no GPU)
+    and prints one JSON line with the metric, the reference marker, the
+    cpu_baseline description and an e2e entry without host-device bytes."""
+    import json
+    r = _run_bench(["--impl", "reference", "--steps", "2", "--warmup", "3"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC
+    assert d["unit"] == "trials/s" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["steps"] == 2 and d["warmup"] == 3 and d["dtype"] == "f64"
+    assert d["config"]["workload"] == bench.WORKLOAD and d["config"]["N"] == 1 << 23
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": "trials/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    r = _run_bench(["--impl", "reference", "--steps", "2", "--warmup", "3"],
+                   env_extra={"RANK": "1", "WORLD_SIZE": "2"}, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == ""
