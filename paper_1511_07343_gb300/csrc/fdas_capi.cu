@@ -267,7 +267,7 @@ int ensure_lane(fdas_plan* p) {
     if (!rc) rc = dalloc(l, &l->cands, (size_t)p->max_cands);
     if (!rc) rc = dalloc(l, &l->count, 1);
     if (!rc) rc = dalloc(l, &l->hs_list, (size_t)kHsListCap);
-    if (!rc) rc = dalloc(l, &l->hs_nlist, 1);
+    if (!rc) rc = dalloc(l, &l->hs_nlist, 2);
     if (!rc)
       rc = cuda_check(cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking), "lane stream");
     if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming), "event");
@@ -530,7 +530,7 @@ int fdas_plan_create(fdas_plan** out, int64_t N, int32_t zmax, int32_t dz, int32
   TRY(dalloc(p, &p->cands, (size_t)max_cands));
   TRY(dalloc(p, &p->count, 1));
   TRY(dalloc(p, &p->hs_list, (size_t)fdas::kHsListCap));
-  TRY(dalloc(p, &p->hs_nlist, 1));
+  TRY(dalloc(p, &p->hs_nlist, 2));
   TRY(make_hs_order(p));
 
   cudaStream_t s = p->stream;

@@ -15,6 +15,8 @@ namespace fdas {
 namespace {
 
 constexpr int kNT = 256;
+// pairs per chunk of the correlation's dynamically shared tail
+constexpr int kChunk = 8;
 
 // Step 3 + step 4: gather segment s (zero-filled at the spectrum edges) and
 // FFT it forward; seg[s][k] in natural order.
@@ -69,8 +71,9 @@ __host__ __device__ constexpr int pk_ra2() { return L / 512; }
 // memory for the whole
 // sweep over templates; template spectra stream from L2. Besides the plane
 // row the kernel writes the 4-bin maxima Q4[z][r/4] (used to screen the
-// harmonic sums) and emits the h = 1 candidates. Each CTA takes an evenly
-// split, contiguous range of (segment, template) pairs (one wave).
+// harmonic sums) and emits the h = 1 candidates. One wave of CTAs; each takes
+// a contiguous range of 3/4 of the (segment, template) pairs split evenly,
+// then chunks of the rest from a device counter.
 template <int L>
 struct Corr {
   static constexpr int T = L / 32;
@@ -123,7 +126,8 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
     k_correlate_fused(const float4* __restrict__ seg4, const float4* __restrict__ bank4,
                       float* __restrict__ plane, float* __restrict__ q4, int64_t nb, int Z, int V,
                       int m, int64_t n_pairs, const float2* __restrict__ twL, float thr1,
-                      fdas_cand* __restrict__ cands, unsigned long long* count, int64_t maxc) {
+                      fdas_cand* __restrict__ cands, unsigned long long* count, int64_t maxc,
+                      unsigned long long* next) {
   constexpr int ib = IB;
   using C = Corr<L>;
   constexpr int T = C::T, NA = C::NA, RA2 = C::RA2, NB2 = C::NB2;
@@ -139,10 +143,10 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
   // Integer-bin planes with m % 16 == 0 leave the kernel by bulk copies: the
   // valid slice of the power row (Ps + m/2, 4 nvalid bytes) and its 4-bin
   // maxima (Q4s, nvalid bytes), both 16-byte aligned at either end. Thread 0
-  // issues the copies of pair p after the first CTA barrier of pair p + 1
-  // (every thread has fenced its shared-memory writes of pair p before it)
-  // and waits until they have read shared memory before the second one,
-  // after which pair p + 1 rewrites Ps and Q4s.
+  // issues the copies of a pair after the first CTA barrier of the next pair
+  // the CTA does (every thread has fenced its shared-memory writes of the
+  // pair before it) and waits until they have read shared memory before the
+  // second one, after which the next pair rewrites Ps and Q4s.
   const bool bulk = IB == 0 && (m % 16) == 0;
   auto issue_bulk = [&](int64_t pp) {  // pair pp's row slice (thread 0)
     const int ps = (int)(pp / Z);
@@ -192,161 +196,183 @@ __global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
   const int u1 = tid & 15, a1 = tid >> 4;  // A1 role
   const int half_m = m / 2;
   const int64_t nq = nb >> 2;
-  const int64_t p0 = (int64_t)blockIdx.x * n_pairs / gridDim.x;
-  const int64_t p1 = (int64_t)(blockIdx.x + 1) * n_pairs / gridDim.x;
+  // The first 3/4 of the pairs are split evenly in contiguous ranges, one
+  // per CTA (the segment spectrum is reloaded only when the segment
+  // changes); the rest go out in chunks of kChunk consecutive pairs from the
+  // counter `next` (zeroed before the launch), so that CTAs on SMs that run
+  // faster take more of the tail. Thread 0 claims the next chunk during the
+  // last pair of a range, before that pair's first CTA barrier; the claim is
+  // read after the range, and its slot alternates with the range parity.
+  const int64_t nstat = n_pairs * 3 / 4 / kChunk * kChunk;
+  const int64_t ndyn = (n_pairs - nstat + kChunk - 1) / kChunk;
+  __shared__ int64_t s_next[2];
   int s_cur = -1;
-  for (int64_t p = p0; p < p1; ++p) {
-    const int s = (int)(p / Z);
-    const int z = (int)(p - (int64_t)s * Z);
-    if (s != s_cur) {  // segment spectrum -> tensor memory columns 0..63
-      const float4* fs = seg4 + (size_t)s * L2 + a1 * 16 + u1;
+  int64_t p_prev = -1;  // the last pair done, whose row slice is not yet copied out
+  int64_t chunk = -1;   // -1: this CTA's static range
+  for (int k = 0; chunk < ndyn; ++k) {
+    const int64_t q0 = chunk < 0 ? (int64_t)blockIdx.x * nstat / gridDim.x : nstat + chunk * kChunk;
+    const int64_t q1 =
+        chunk < 0 ? (int64_t)(blockIdx.x + 1) * nstat / gridDim.x : min(q0 + kChunk, n_pairs);
+    if (q1 <= q0) {  // an empty static range claims its first chunk here
+      if (tid == 0) s_next[k & 1] = (int64_t)atomicAdd(next, 1ull);
+      __syncthreads();
+    }
+    for (int64_t p = q0; p < q1; ++p) {
+      if (tid == 0 && p == q1 - 1) s_next[k & 1] = (int64_t)atomicAdd(next, 1ull);
+      const int s = (int)(p / Z);
+      const int z = (int)(p - (int64_t)s * Z);
+      if (s != s_cur) {  // segment spectrum -> tensor memory columns 0..63
+        const float4* fs = seg4 + (size_t)s * L2 + a1 * 16 + u1;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float f[16];
+        for (int q = 0; q < 4; ++q) {
+          float f[16];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float4 v = __ldg(fs + (q * 4 + i) * RA2 * 16);
-          f[4 * i] = v.x;
-          f[4 * i + 1] = v.y;
-          f[4 * i + 2] = v.z;
-          f[4 * i + 3] = v.w;
+          for (int i = 0; i < 4; ++i) {
+            const float4 v = __ldg(fs + (q * 4 + i) * RA2 * 16);
+            f[4 * i] = v.x;
+            f[4 * i + 1] = v.y;
+            f[4 * i + 2] = v.z;
+            f[4 * i + 3] = v.w;
+          }
+          tmem_st16(tbase + 16 * q, f);
         }
-        tmem_st16(tbase + 16 * q, f);
+        tmem_wait_st();
+        s_cur = s;
       }
-      tmem_wait_st();
-      s_cur = s;
-    }
-    // ---- A1
-    c2 v[16];
-    const float4* tz = bank4 + (size_t)z * L2 + a1 * 16 + u1;
+      // ---- A1
+      c2 v[16];
+      const float4* tz = bank4 + (size_t)z * L2 + a1 * 16 + u1;
 #pragma unroll
-    // (L2 only: the shared-memory carve-out leaves L1 too small to keep
-    // a 64 KB template row; measured 1% faster than the read-only path)
-    for (int b = 0; b < 16; ++b) v[b] = c2_of(__ldcg(tz + b * RA2 * 16));
+      // (L2 only: the shared-memory carve-out leaves L1 too small to keep
+      // a 64 KB template row; measured 1% faster than the read-only path)
+      for (int b = 0; b < 16; ++b) v[b] = c2_of(__ldcg(tz + b * RA2 * 16));
 #pragma unroll
-    for (int q = 0; q < 4; q += 2) {
-      float f[32];
-      tmem_ld16x2(tbase + 16 * q, tbase + 16 * q + 16, f);
+      for (int q = 0; q < 4; q += 2) {
+        float f[32];
+        tmem_ld16x2(tbase + 16 * q, tbase + 16 * q + 16, f);
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
-        v[q * 4 + i] = c2_mul(v[q * 4 + i], c2{make_float2(f[4 * i], f[4 * i + 1]),
-                                              make_float2(f[4 * i + 2], f[4 * i + 3])});
-    }
-    dft_pairs<16, kInv>(v);
-#pragma unroll
-    for (int c = 1; c < 16; ++c) {
-      const float4 tw = twA[a1 * 17 + c];
-      v[brev<16>(c)] = c2_mul_cs(v[brev<16>(c)], make_float2(tw.x, tw.y), make_float2(tw.z, tw.w));
-    }
-#pragma unroll
-    for (int c = 0; c < 16; ++c) X[xsw(a1 * 16 + c, u1)] = f4_of(v[brev<16>(c)]);
-    __syncthreads();
-    if (bulk && tid == 0 && p > p0) issue_bulk(p - 1);  // the previous pair's row slice
-    // ---- A2
-    c2 w[NB2][RA2];
-#pragma unroll
-    for (int i = 0; i < NB2; ++i) {
-      const int g = tid + T * i;
-      const int u = g & 15, c = g >> 4;
-#pragma unroll
-      for (int a = 0; a < RA2; ++a) w[i][a] = c2_of(X[xsw(a * 16 + c, u)]);
-    }
-    // (no barrier: each thread writes its results into the slots it read)
-#pragma unroll
-    for (int i = 0; i < NB2; ++i) {
-      dft_pairs<RA2, kInv>(w[i]);
-      const int g = tid + T * i;
-      const int u = g & 15, c = g >> 4;
-#pragma unroll
-      for (int d0 = 0; d0 < RA2; d0 += 4) {
-        float f[16];
-        tmem_ld16(tbase + 64 + 4 * (i * RA2 + d0), f);
-#pragma unroll
-        for (int dd = 0; dd < 4; ++dd) {
-          const int d = d0 + dd;
-          const c2 t = c2_mul_cs(w[i][brev<RA2>(d)], make_float2(f[4 * dd], f[4 * dd + 1]),
-                                 make_float2(f[4 * dd + 2], f[4 * dd + 3]));
-          X[xsw(16 * d + c, u)] = f4_of(t);
-        }
+        for (int i = 0; i < 8; ++i)
+          v[q * 4 + i] = c2_mul(v[q * 4 + i], c2{make_float2(f[4 * i], f[4 * i + 1]),
+                                                make_float2(f[4 * i + 2], f[4 * i + 3])});
       }
-    }
-    // the copies of the previous pair's row slice have read Ps and Q4s
-    if (bulk && tid == 0 && p > p0) bulk_wait_read();
-    __syncthreads();
-    // ---- B
-    c2 y[16];
+      dft_pairs<16, kInv>(v);
 #pragma unroll
-    for (int u = 0; u < 16; ++u) y[u] = c2_of(X[xsw(tid, u)]);
-    // every warp has read X: the next pair's A1 may overwrite it
-    __syncthreads();
-    // every output goes to Ps[n] (room for all L); the valid V start at half_m
-    dft32_dit<kInv>(y, [&](int e, float2 o) { Ps[tid + NA * e] = cnorm(o); });
-    // Outputs n .. n+3 (n % 4 == 0) come from threads n % NA .. +3, lanes of
-    // one warp; so each warp stores the float4s its own lanes produced and a
-    // warp barrier suffices (the next pair writes Ps only after its first
-    // CTA barrier, which every warp reaches after this output stage).
-    __syncwarp();
-    // coalesced float4 stores of the plane row slice, its 4-bin maxima and
-    // the h = 1 candidates; r = s V + i, i < V, r < nb
-    const int64_t r0 = (int64_t)s * V;
-    int64_t nvalid = nb - r0;
-    if (nvalid > V) nvalid = V;
-    const int nhi = half_m + (int)nvalid;  // valid outputs n in [half_m, nhi), multiples of 4 apart
-    // (half-bin planes, ib = 1: template row z = 2j + e fills columns 2r + e
-    // of plane row j; rows 2j and 2j+1 are consecutive pairs, so each sector
-    // is completed in L2 before it is written back)
-    float* prow = plane ? plane + (size_t)(z >> ib) * (nb << ib) + (r0 << ib) + (z & ib) : nullptr;
-    float* qrow = q4 ? q4 + (size_t)z * nq + (r0 >> 2) : nullptr;
-    const float4* P4 = reinterpret_cast<const float4*>(Ps);
-    const int lane = tid & 31;
-    // lane: 4 outputs starting at n = NA j + 32 warp + 4 (lane % 8), j = lane / 8 + 4 i
-    const int nw = 32 * warp + 4 * (lane & 7);
-    bool hit = false;
+      for (int c = 1; c < 16; ++c) {
+        const float4 tw = twA[a1 * 17 + c];
+        v[brev<16>(c)] = c2_mul_cs(v[brev<16>(c)], make_float2(tw.x, tw.y), make_float2(tw.z, tw.w));
+      }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int n = NA * ((lane >> 3) + 4 * i) + nw;
-      if (n >= half_m && n < nhi) {
-        const float4 p4 = P4[n >> 2];
-        const int k = (n - half_m) >> 2;  // float4 index in the row slice
-        const float mx = fmaxf(fmaxf(p4.x, p4.y), fmaxf(p4.z, p4.w));
-        if (bulk) {
-          Q4s[k] = mx;  // the plane row itself leaves from Ps
-        } else if (prow) {
-          if constexpr (IB) {
-            prow[8 * k] = p4.x;
-            prow[8 * k + 2] = p4.y;
-            prow[8 * k + 4] = p4.z;
-            prow[8 * k + 6] = p4.w;
-          } else {
-            reinterpret_cast<float4*>(prow)[k] = p4;
+      for (int c = 0; c < 16; ++c) X[xsw(a1 * 16 + c, u1)] = f4_of(v[brev<16>(c)]);
+      __syncthreads();
+      if (bulk && tid == 0 && p_prev >= 0) issue_bulk(p_prev);  // the previous pair's row slice
+      // ---- A2
+      c2 w[NB2][RA2];
+#pragma unroll
+      for (int i = 0; i < NB2; ++i) {
+        const int g = tid + T * i;
+        const int u = g & 15, c = g >> 4;
+#pragma unroll
+        for (int a = 0; a < RA2; ++a) w[i][a] = c2_of(X[xsw(a * 16 + c, u)]);
+      }
+      // (no barrier: each thread writes its results into the slots it read)
+#pragma unroll
+      for (int i = 0; i < NB2; ++i) {
+        dft_pairs<RA2, kInv>(w[i]);
+        const int g = tid + T * i;
+        const int u = g & 15, c = g >> 4;
+#pragma unroll
+        for (int d0 = 0; d0 < RA2; d0 += 4) {
+          float f[16];
+          tmem_ld16(tbase + 64 + 4 * (i * RA2 + d0), f);
+#pragma unroll
+          for (int dd = 0; dd < 4; ++dd) {
+            const int d = d0 + dd;
+            const c2 t = c2_mul_cs(w[i][brev<RA2>(d)], make_float2(f[4 * dd], f[4 * dd + 1]),
+                                   make_float2(f[4 * dd + 2], f[4 * dd + 3]));
+            X[xsw(16 * d + c, u)] = f4_of(t);
           }
         }
-        if (qrow && !bulk) qrow[k] = mx;
-        hit |= mx >= thr1;
       }
-    }
-    if (cands && __any_sync(0xffffffffu, hit)) {
-      // rare: some power this warp stored reached T_1; the warp scans its
-      // own float4s again and appends
-#pragma unroll 1
+      // the copies of the previous pair's row slice have read Ps and Q4s
+      if (bulk && tid == 0 && p_prev >= 0) bulk_wait_read();
+      __syncthreads();
+      // ---- B
+      c2 y[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) y[u] = c2_of(X[xsw(tid, u)]);
+      // every warp has read X: the next pair's A1 may overwrite it
+      __syncthreads();
+      // every output goes to Ps[n] (room for all L); the valid V start at half_m
+      dft32_dit<kInv>(y, [&](int e, float2 o) { Ps[tid + NA * e] = cnorm(o); });
+      // Outputs n .. n+3 (n % 4 == 0) come from threads n % NA .. +3, lanes of
+      // one warp; so each warp stores the float4s its own lanes produced and a
+      // warp barrier suffices (the next pair writes Ps only after its first
+      // CTA barrier, which every warp reaches after this output stage).
+      __syncwarp();
+      // coalesced float4 stores of the plane row slice, its 4-bin maxima and
+      // the h = 1 candidates; r = s V + i, i < V, r < nb
+      const int64_t r0 = (int64_t)s * V;
+      int64_t nvalid = nb - r0;
+      if (nvalid > V) nvalid = V;
+      const int nhi = half_m + (int)nvalid;  // valid outputs n in [half_m, nhi), multiples of 4 apart
+      // (half-bin planes, ib = 1: template row z = 2j + e fills columns 2r + e
+      // of plane row j; rows 2j and 2j+1 are consecutive pairs, so each sector
+      // is completed in L2 before it is written back)
+      float* prow = plane ? plane + (size_t)(z >> ib) * (nb << ib) + (r0 << ib) + (z & ib) : nullptr;
+      float* qrow = q4 ? q4 + (size_t)z * nq + (r0 >> 2) : nullptr;
+      const float4* P4 = reinterpret_cast<const float4*>(Ps);
+      const int lane = tid & 31;
+      // lane: 4 outputs starting at n = NA j + 32 warp + 4 (lane % 8), j = lane / 8 + 4 i
+      const int nw = 32 * warp + 4 * (lane & 7);
+      bool hit = false;
+#pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int n = NA * ((lane >> 3) + 4 * i) + nw;
-        const bool in = n >= half_m && n < nhi;
-        const float4 p4 = in ? P4[n >> 2] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const int rk = (int)(r0 + (n - half_m));
-        emit(in && rk >= 1 && p4.x >= thr1, rk, z, 1, p4.x, cands, count, maxc);
-        emit(in && p4.y >= thr1, rk + 1, z, 1, p4.y, cands, count, maxc);
-        emit(in && p4.z >= thr1, rk + 2, z, 1, p4.z, cands, count, maxc);
-        emit(in && p4.w >= thr1, rk + 3, z, 1, p4.w, cands, count, maxc);
+        if (n >= half_m && n < nhi) {
+          const float4 p4 = P4[n >> 2];
+          const int k = (n - half_m) >> 2;  // float4 index in the row slice
+          const float mx = fmaxf(fmaxf(p4.x, p4.y), fmaxf(p4.z, p4.w));
+          if (bulk) {
+            Q4s[k] = mx;  // the plane row itself leaves from Ps
+          } else if (prow) {
+            if constexpr (IB) {
+              prow[8 * k] = p4.x;
+              prow[8 * k + 2] = p4.y;
+              prow[8 * k + 4] = p4.z;
+              prow[8 * k + 6] = p4.w;
+            } else {
+              reinterpret_cast<float4*>(prow)[k] = p4;
+            }
+          }
+          if (qrow && !bulk) qrow[k] = mx;
+          hit |= mx >= thr1;
+        }
       }
+      if (cands && __any_sync(0xffffffffu, hit)) {
+        // rare: some power this warp stored reached T_1; the warp scans its
+        // own float4s again and appends
+#pragma unroll 1
+        for (int i = 0; i < 8; ++i) {
+          const int n = NA * ((lane >> 3) + 4 * i) + nw;
+          const bool in = n >= half_m && n < nhi;
+          const float4 p4 = in ? P4[n >> 2] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const int rk = (int)(r0 + (n - half_m));
+          emit(in && rk >= 1 && p4.x >= thr1, rk, z, 1, p4.x, cands, count, maxc);
+          emit(in && p4.y >= thr1, rk + 1, z, 1, p4.y, cands, count, maxc);
+          emit(in && p4.z >= thr1, rk + 2, z, 1, p4.z, cands, count, maxc);
+          emit(in && p4.w >= thr1, rk + 3, z, 1, p4.w, cands, count, maxc);
+        }
+      }
+      // this thread's Ps and Q4s writes, visible to the bulk copies
+      if (bulk) fence_proxy_async_shared();
+      p_prev = p;
     }
-    // this thread's Ps and Q4s writes, visible to the bulk copies
-    if (bulk) fence_proxy_async_shared();
+    chunk = s_next[k & 1];
   }
   if (bulk) {  // the last pair's row slice
     __syncthreads();
-    if (tid == 0 && p1 > p0) {
-      issue_bulk(p1 - 1);
+    if (tid == 0 && p_prev >= 0) {
+      issue_bulk(p_prev);
       bulk_wait_all();
     }
   }
@@ -423,10 +449,13 @@ int corr_launch(fdas_plan* p, float* plane, float* q4, fdas_cand* cands,
   int64_t grid = (int64_t)occ * sms;
   if (grid > n_pairs) grid = n_pairs;
   p->corr_grid = (int)grid;
+  e = cudaMemsetAsync(p->hs_nlist + 1, 0, sizeof(unsigned long long), p->stream);
+  if (e != cudaSuccess) return cuda_check(e, "clear the pair counter");
   k_correlate_fused<L, IB><<<(unsigned)grid, C::T, smem, p->stream>>>(
       reinterpret_cast<const float4*>(p->seg),
       reinterpret_cast<const float4*>(ib ? p->bank_ib : p->bank), plane, ib ? nullptr : q4, p->nb,
-      zrows, p->V, p->m, n_pairs, p->tw_L, p->thr[0], ib ? nullptr : cands, count, p->max_cands);
+      zrows, p->V, p->m, n_pairs, p->tw_L, p->thr[0], ib ? nullptr : cands, count, p->max_cands,
+      p->hs_nlist + 1);
   return cuda_check(cudaGetLastError(), "k_correlate_fused");
 }
 

@@ -49,6 +49,8 @@ struct fdas_plan {
   // pairs of top bins the harmonic-sum screen flags, (j << 32) | r, for the
   // exact sums (kHsListCap entries; flags past the capacity are summed inline)
   unsigned long long* hs_list = nullptr;
+  // [0] entries in hs_list, [1] the correlation's next chunk of pairs (each
+  // zeroed on the stream before the kernel that counts it)
   unsigned long long* hs_nlist = nullptr;
   // launch order of the screen's tiles for 256- and 32-thread blocks, made
   // for plane width hs_order_w (see make_hs_order)
