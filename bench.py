@@ -44,7 +44,7 @@ FP32_LANES_PER_SM = 128
 # (A 2^21-sample capture, one launch per kernel, scaled to the 2^23-sample
 # launch by the (segment, template) pairs or top bins it processes.)
 MEASURED_TRAFFIC = {
-    "k_correlate_fused": (4.055e+09, "paper_1511_07343_gb300/csrc/fdas_correlate.cu", "4144d903fae2338e"),
+    "k_correlate_fused": (4.055e+09, "paper_1511_07343_gb300/csrc/fdas_correlate.cu", "5095bcf9f5860ca7"),
     "k_harmsum_staged": (8.457e+08, "paper_1511_07343_gb300/csrc/fdas_harmsum.cu", "03294e1f8c59e47a"),
 }
 

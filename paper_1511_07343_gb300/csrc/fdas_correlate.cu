@@ -85,7 +85,11 @@ struct Corr {
   static constexpr int NGROUPS = (NW + 3) / 4;  // warps w and w + 4 share TMEM lanes
   static constexpr int NCOLS = 128 * NGROUPS;   // per thread: 64 (F) + 64 (B twiddles)
   static constexpr int MAXCTA = 512 / NCOLS;
-  static constexpr int MINB = L == 8192 ? 2 : 4;
+  // registers per thread: two (L = 8192) or four CTAs per SM leave 4 K of the
+  // SM's 64 K registers free, room for a warp of another trial lane's
+  // harmonic-sum screen beside them (measured 0.8% faster alone, 0.5% per
+  // lane-overlapped trial, against 128; 112 spills)
+  static constexpr int MAXREG = 120;
   // exchange buffer, A1 twiddles, power row (L floats), 4-bin maxima row (L/4)
   static constexpr size_t SMEM = 16 * (size_t)(XF4 + RA2 * 17) + 4 * (size_t)L + (size_t)L;
 };
@@ -122,7 +126,7 @@ FDAS_DEV c2 c2_of(float4 v) { return c2{make_float2(v.x, v.y), make_float2(v.z, 
 FDAS_DEV float4 f4_of(c2 v) { return make_float4(v.re.x, v.re.y, v.im.x, v.im.y); }
 
 template <int L, int IB>
-__global__ void __launch_bounds__(Corr<L>::T, Corr<L>::MINB)
+__global__ void __maxnreg__(Corr<L>::MAXREG)
     k_correlate_fused(const float4* __restrict__ seg4, const float4* __restrict__ bank4,
                       float* __restrict__ plane, float* __restrict__ q4, int64_t nb, int Z, int V,
                       int m, int64_t n_pairs, const float2* __restrict__ twL, float thr1,
