@@ -158,11 +158,13 @@ int dispatch_rows(fdas_plan* p, const float2* T, float2* Zo) {
 // k ([k-32, k+31] shifted into [1, nb-1]); Xw_k = X_k sqrt(ln2 / mu_k).
 // One warp takes 64 consecutive bins (a tile); no CTA barrier is used.
 //  1. The union of the tile's windows (at most 127 bins from u0) is loaded
-//     as 128 exact 64-bit keys (power bits, entry index; powers are >= 0, so
-//     their bit patterns order like their values, and entries past the
-//     spectrum get the largest keys) and sorted by a bitonic network in
+//     as 128 keys, the power's bit pattern (powers are >= 0, so the patterns
+//     order like the values; entries past the spectrum get the largest key),
+//     each carrying its entry index, and sorted by a bitonic network in
 //     registers: slot i = 4 lane + w, compare-exchanges at distance 1 and 2
-//     inside a lane, at distance >= 4 through shuffles.
+//     inside a lane, at distance >= 4 through shuffles. Ties need no order:
+//     equal powers are equal order statistics, and a compare-exchange moves
+//     or keeps both of its entries, so the slots stay a permutation.
 //  2. pos[e] = sorted slot of entry e. The window of offset o (entries
 //     o .. o+63) is the 128-bit mask M(o) of the slots its entries hold:
 //     M(0) is an XOR reduction of the bits of entries 0..63 over the warp,
@@ -251,8 +253,10 @@ __global__ void __launch_bounds__(32 * kWWarps) k_whiten(const float2* __restric
         for (int w = 0; w < 4; ++w) {
           const unsigned oh = __shfl_xor_sync(0xffffffffu, kh[w], ld);
           const unsigned ol = __shfl_xor_sync(0xffffffffu, kl[w], ld);
-          const bool other_less = oh < kh[w] || (oh == kh[w] && ol < kl[w]);
-          if (other_less == keep_min) {  // keys are distinct (entry index)
+          // strict on both sides: equal powers stay where they are, so every
+          // entry keeps exactly one slot
+          const bool lt = oh < kh[w], gt = kh[w] < oh;
+          if ((lt && keep_min) || (gt && !keep_min)) {
             kh[w] = oh;
             kl[w] = ol;
           }
@@ -263,7 +267,7 @@ __global__ void __launch_bounds__(32 * kWWarps) k_whiten(const float2* __restric
           if (w & d) continue;
           const int v = w | d;
           const bool asc = ((4 * lane + w) & size) == 0;
-          const bool gt = kh[w] > kh[v] || (kh[w] == kh[v] && kl[w] > kl[v]);
+          const bool gt = kh[w] > kh[v];
           if (gt == asc) {
             const unsigned th = kh[w], tl = kl[w];
             kh[w] = kh[v];
