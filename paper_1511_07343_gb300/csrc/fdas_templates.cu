@@ -158,9 +158,6 @@ HD cd template_tap_q2(int zi, long long Q) {
   return mk(t.re / scale, -t.im / scale);
 }
 
-// tau_z(d) for integer z = zi and d = di (float64).
-HD cd template_tap(int zi, int di) { return template_tap_q2(zi, 2LL * di + zi); }
-
 // rows = 1: row j holds tau_{z_j}; rows = 2: row 2j + e holds tau_{z_j} at
 // frequency offset e/2 (the half-bin bank), q = d - e/2 + z/2.
 __global__ void k_template_taps(double2* __restrict__ taps, int Z, int m, int zmax, int dz,
