@@ -117,16 +117,22 @@ def test_spectrum_and_whitening(gpu_lib, logn):
     assert np.max(np.abs(W_gpu - W_orc)) <= 5e-5
 
 
-@pytest.mark.parametrize("N", [1 << 15, 12288])
-def test_whitening_exact_medians_with_ties(gpu_lib, N):
+@pytest.mark.parametrize("N,two", [(1 << 15, False), (12288, False), (1 << 15, True)])
+def test_whitening_exact_medians_with_ties(gpu_lib, N, two):
     """Small-integer spectra make every power exact in float32 and full of
     ties, so the medians are exact order statistics: the whitened spectrum
     must match the oracle to float32 rounding of the scale (N = 12288 gives a
-    tile count that is not a multiple of a CTA's tiles)."""
+    tile count that is not a multiple of a CTA's tiles). With `two` every
+    power is 1 or 2, so most windows hold two long runs of equal keys and
+    the median sits at or between them: a sort that lost or duplicated an
+    entry among equal keys would move it."""
     fd = gpu_lib
     nb = N // 2
     rng = np.random.default_rng(N)
-    X = (rng.integers(1, 4, nb) + 1j * rng.integers(0, 3, nb)).astype(np.complex64)
+    if two:
+        X = np.where(rng.random(nb) < 0.5, 1.0 + 0j, 1.0 + 1j).astype(np.complex64)
+    else:
+        X = (rng.integers(1, 4, nb) + 1j * rng.integers(0, 3, nb)).astype(np.complex64)
     plan = make_plan(fd, N, 20, 2, 64, 2048, 1)
     try:
         spec = torch.from_numpy(X.view(np.float32).copy()).to(DEV)
